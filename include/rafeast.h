@@ -1,0 +1,260 @@
+/*
+ * rafeast.h - C ABI of the GB300 (sm_103a) RA-FEAST hot path.
+ *
+ * RA-FEAST (arXiv 2512.01257) computes every eigenpair of a sparse symmetric
+ * positive definite matrix A whose eigenvalue lies in [lmin, lmax] (Eq. 1):
+ * a randomized warmstart (Algorithm 2, Phase 1) followed by FEAST subspace
+ * iterations (Algorithm 1 / Algorithm 2, Phase 2). Each FEAST iteration
+ * applies the quadrature projector of Eq. 3 by solving the complex symmetric
+ * shifted systems (z_j I - A) X_j = Q for all N_c nodes at once with batched
+ * COCG, accumulates Q~ = sum_j Re(w_j X_j), re-orthonormalises Q~ and runs a
+ * Rayleigh-Ritz step.
+ *
+ * Conventions shared by every entry point:
+ *  - A = L + diag_shift * I, where L is given in CSR form (int32 row_ptr[n+1],
+ *    int32 col_idx[nnz], double values[nnz]) and must be symmetric. Keeping
+ *    the shift out of the CSR keeps integer graph-Laplacian values exact when
+ *    the mixed-precision path rounds them to float32.
+ *  - Dense blocks (subspaces, eigenvectors, Omega) are column-major n x m
+ *    arrays of double in the caller's row order: entry (i, k) is at
+ *    ptr[k * n + i]. The library may reorder rows internally for locality;
+ *    that never shows at this interface.
+ *  - A pointer argument documented "device" must be a CUDA device pointer
+ *    (or managed memory) on the handle's device; "host" means ordinary host
+ *    memory. Inputs are copied or read; the caller keeps ownership of every
+ *    buffer it passes and the library never frees it.
+ *  - Every function returns an int status (RAFEAST_OK = 0; positive values
+ *    are solver outcomes with valid outputs, negative values are errors with
+ *    outputs unspecified). No function aborts the process or throws across
+ *    the ABI. A handle is not thread safe; distinct handles may be used from
+ *    distinct threads and streams.
+ *  - Work is ordered after all prior work on the stream given to
+ *    rafeast_create, and that stream is made to wait for the call's device
+ *    work before the call returns. Calls with host outputs synchronise.
+ */
+#ifndef RAFEAST_H
+#define RAFEAST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes (in the spirit of FEAST's info output) ---------------- */
+#define RAFEAST_OK 0
+#define RAFEAST_NO_EIGENVALUE 1      /* no Ritz value inside [lmin, lmax]     */
+#define RAFEAST_NO_CONVERGENCE 2     /* max_outer reached; best iterate out   */
+#define RAFEAST_M0_TOO_SMALL 3       /* every Ritz value inside: m0 <= count  */
+#define RAFEAST_ERR_INVALID_ARG (-1) /* bad size, pointer, CSR or parameter   */
+#define RAFEAST_ERR_NOT_SYMMETRIC (-2)
+#define RAFEAST_ERR_CUDA (-3)        /* a CUDA runtime call failed            */
+#define RAFEAST_ERR_COCG_BREAKDOWN (-4)
+#define RAFEAST_ERR_TIMEOUT (-5)     /* a bounded device wait ran out         */
+#define RAFEAST_ERR_OUT_OF_MEMORY (-6)
+#define RAFEAST_ERR_NOT_READY (-7)   /* e.g. START_SUBSPACE with no subspace  */
+#define RAFEAST_ERR_CHOLESKY (-8)    /* Cholesky-QR failed even when shifted  */
+#define RAFEAST_ERR_NO_DEVICE (-9)
+
+/* ---- enums --------------------------------------------------------------- */
+#define RAFEAST_FP64 0   /* every step in double                              */
+#define RAFEAST_MIXED 1  /* shifted solves + their SpMM in float32; Gram,      *
+                          * Cholesky-QR, Rayleigh-Ritz, residuals in double    */
+
+#define RAFEAST_FORM_DIRECT 0     /* COCG right-hand side Q (as printed)      */
+#define RAFEAST_FORM_CORRECTION 1 /* COCG right-hand side A Q - Q diag(theta); *
+                                   * X_j rebuilt as (Q + Y_j)/(z_j - theta):   *
+                                   * the same X_j, with an inexact solve's    *
+                                   * error proportional to the residual       */
+
+#define RAFEAST_START_RANDOM 0   /* Algorithm 1: random orthonormal Q(0)      */
+#define RAFEAST_START_SUBSPACE 1 /* the handle's subspace (warmstart / set)   */
+
+#define RAFEAST_CREATE_NO_REORDER 1u      /* keep the caller's row order      */
+#define RAFEAST_CREATE_FORCE_REORDER 2u   /* always apply the RCM order       */
+#define RAFEAST_CREATE_CHECK_SYMMETRY 4u  /* O(nnz) host check, -2 on failure */
+
+/* option keys for rafeast_set_option */
+#define RAFEAST_OPT_WARMSTART_MAP 1 /* 0 auto, 1 literal (A-lmin)/(lmax-lmin), *
+                                     * 2 low-end (g I - A)/(g - lmin)          */
+#define RAFEAST_OPT_CHUNK 2         /* COCG iterations per CUDA-graph replay   */
+#define RAFEAST_OPT_AUTOTUNE 3      /* 1 (default) time SpMM shapes, 0 off     */
+#define RAFEAST_OPT_LANES 4         /* force lanes per row (4,8,16,32), 0 auto */
+
+typedef struct rafeast_ctx* rafeast_t;
+
+/* Solver parameters (all host). Field order is part of the ABI. */
+typedef struct rafeast_params {
+  double lmin, lmax;     /* search interval, lmin < lmax                      */
+  int32_t m0;            /* subspace size, 1..1024, >= eigenvalues inside     */
+  int32_t nc;            /* quadrature nodes on the half contour, 1..16        */
+  double ellipse_ratio;  /* imaginary/real semi-axis ratio e, (0, 1]           */
+  double solve_tol;      /* COCG: stop when ||r||_2 <= solve_tol * ||b||_2     */
+  double outer_tol;      /* stop when max in-interval ||Av-lv||/||A||_1 <= tol */
+  int32_t max_outer;     /* FEAST iterations cap (Algorithm 2: max_iter)       */
+  int32_t max_inner;     /* COCG iterations cap per solve                      */
+  int32_t precision;     /* RAFEAST_FP64 or RAFEAST_MIXED                      */
+  int32_t solve_form;    /* RAFEAST_FORM_DIRECT or RAFEAST_FORM_CORRECTION     */
+  int32_t start;         /* RAFEAST_START_RANDOM or RAFEAST_START_SUBSPACE     */
+  int32_t reserved;      /* must be 0                                          */
+  uint64_t seed;         /* seed of the random start (RAFEAST_START_RANDOM)    */
+} rafeast_params;
+
+/* Diagnostics filled by rafeast_solve / rafeast_filter (may be NULL). */
+typedef struct rafeast_info {
+  int32_t status;
+  int32_t outer_iters;       /* FEAST iterations run                          */
+  int32_t cocg_iters_total;  /* sum over iterations of the slowest system     */
+  int32_t cocg_min_last;     /* last iteration: fewest COCG steps of a system */
+  int32_t cocg_max_last;     /* last iteration: most COCG steps of a system   */
+  int32_t cholqr_shifted;    /* Cholesky-QR passes that needed a shift        */
+  int32_t kernel_launches;   /* kernels launched by this call                 */
+  int32_t spmm_launches;     /* of which sparse-matrix products               */
+  double max_resid;          /* max in-interval relative residual             */
+  double t_warmstart_ms;     /* device time per phase (CUDA events)           */
+  double t_filter_ms;
+  double t_orth_ms;
+  double t_rr_ms;
+  double t_total_ms;
+} rafeast_info;
+
+/* ---- handle ------------------------------------------------------------- */
+
+/* Create a solver for A = L + diag_shift*I (Eq. 1's symmetric positive
+ * definite A; Section 5.1's graph Laplacians L = D - W with a shift).
+ * row_ptr/col_idx/values are host pointers, or device pointers when
+ * inputs_on_device != 0; they are copied and may be freed on return.
+ * Column indices must lie in [0, n) and be sorted within each row; L must be
+ * symmetric (checked only with RAFEAST_CREATE_CHECK_SYMMETRY). stream is a
+ * cudaStream_t (NULL = legacy default stream) on the current device; flags
+ * combine RAFEAST_CREATE_*. On success *out owns every device buffer the
+ * library allocates for this matrix until rafeast_destroy. Errors: -1 for
+ * n <= 0, nnz < 0, a NULL pointer or an invalid CSR; -2 for an asymmetric L
+ * when checked; -6 when device memory runs out; -9 without a CUDA device. */
+int rafeast_create(rafeast_t* out, int64_t n, int64_t nnz,
+                   const int32_t* row_ptr, const int32_t* col_idx,
+                   const double* values, double diag_shift,
+                   int inputs_on_device, void* stream, uint32_t flags);
+
+/* Release the handle and all its device memory. NULL is a no-op. */
+void rafeast_destroy(rafeast_t h);
+
+/* Static English text for a status code. */
+const char* rafeast_status_string(int status);
+
+/* Set a tuning option (RAFEAST_OPT_*). -1 for an unknown key or value. */
+int rafeast_set_option(rafeast_t h, int key, int64_t value);
+
+/* Matrix facts: n, internal reorder flag (1 when rows are permuted), ||A||_1
+ * and the Gershgorin interval of A. Any output pointer may be NULL. */
+int rafeast_matrix_info(rafeast_t h, int64_t* n, int* reordered,
+                        double* norm1, double* gersh_lo, double* gersh_hi);
+
+/* ---- hot-path steps ------------------------------------------------------ */
+
+/* Quadrature nodes and weights on the upper half of the ellipse around
+ * [lmin, lmax] (Section 2.1, Eq. 3): z_j = c + R(cos t_j + i e sin t_j),
+ * w_j = (R om_j/2)(e cos t_j + i sin t_j), t_j = (pi/2)(1 + x_j) with
+ * Gauss-Legendre points x_j and weights om_j; the projector is
+ * Re sum_j w_j (z_j I - A)^{-1}. z and w are host arrays of 2*nc doubles
+ * (re, im interleaved). -1 unless lmin < lmax, 1 <= nc <= 64, 0 < e <= 1. */
+int rafeast_quadrature(double lmin, double lmax, int nc, double e,
+                       double* z, double* w);
+
+/* Raw Philox-4x64-10 words (Salmon et al., SC'11) for counters
+ * (first_block + b, 0, 0, 0), b < nblocks, key (seed, 0): words[4b + t].
+ * words is a device array of 4*nblocks uint64; stream a cudaStream_t. This is
+ * the generator behind Omega (Algorithm 2, "Draw Omega"). */
+int rafeast_philox(uint64_t seed, uint64_t first_block, int64_t nblocks,
+                   uint64_t* words, void* stream);
+
+/* Omega ~ N(0,1)^{n x k} (Algorithm 2; Assumption 1.6) from the Philox
+ * words by Box-Muller; column-major linear index e = c*n + i, block e/4.
+ * omega: device, n*k doubles, caller row order. */
+int rafeast_draw_omega(rafeast_t h, uint64_t seed, int k, double* omega);
+
+/* Y = alpha * (A X) + beta * X for k columns (the SpMM of every power step of
+ * the warmstart, Algorithm 2 Phase 1, and of Rayleigh-Ritz). X, Y: device,
+ * column-major n x k. precision RAFEAST_FP64 computes in double;
+ * RAFEAST_MIXED rounds X and the CSR values to float32 and accumulates in
+ * float32 (the inner-solve kernel's arithmetic). */
+int rafeast_spmm(rafeast_t h, int k, double alpha, double beta,
+                 const double* X, double* Y, int precision);
+
+/* W_j = (z_j I - A) P_j for nc complex shifts and m complex columns
+ * (the operator of the shifted systems of Algorithm 1). P, W: device arrays
+ * of n*m*nc complex values as (re, im) double pairs, entry (i, col, j) at
+ * 2*((col*nc + j)*n + i). z: host, 2*nc doubles. precision as rafeast_spmm. */
+int rafeast_shifted_spmm(rafeast_t h, int nc, const double* z, int m,
+                         const double* P, double* W, int precision);
+
+/* One quadrature filter application (Algorithm 1 "Compute Q~",
+ * Algorithm 2 Step 2a): for every node solve (z_j I - A) X_j = Q by batched
+ * COCG to prm->solve_tol (cap prm->max_inner) in prm->precision and form
+ * Qt = sum_j Re(w_j X_j) in double. Uses prm->lmin, lmax, nc,
+ * ellipse_ratio, solve_form. Q, Qt: device, n x m0 column-major (m0 =
+ * prm->m0). theta: host array of m0 Ritz values for the correction form
+ * (NULL = Rayleigh quotients of Q). -4 on a COCG breakdown. */
+int rafeast_filter(rafeast_t h, const rafeast_params* prm, const double* Q,
+                   const double* theta, double* Qt, rafeast_info* info);
+
+/* Orthonormalise in place, Q R = Q~ (Algorithm 1 QR step), by Cholesky-QR
+ * in double, repeated (CholQR2) and shifted when the Gram matrix is not
+ * numerically positive definite (shifted CholQR3). Q: device n x m in/out.
+ * R: host m x m column-major upper-triangular factor, or NULL. -8 when the
+ * block is rank deficient beyond what a shift repairs. */
+int rafeast_orthonormalize(rafeast_t h, int m, double* Q, double* R);
+
+/* Rayleigh-Ritz (Algorithm 1): A_Q = Q^T A Q = V L V^T with L ascending,
+ * Q <- Q V in place; theta (host, m) receives L and resid (host, m, may be
+ * NULL) the relative residuals ||A q_i - l_i q_i||_2 / ||A||_1. Q must have
+ * orthonormal columns. Q: device n x m. */
+int rafeast_rayleigh_ritz(rafeast_t h, int m, double* Q, double* theta,
+                          double* resid);
+
+/* Randomized warmstart (Algorithm 2 Phase 1; Eq. 6 applied to B): draw
+ * Omega (n x (m0+p)) from seed, Y = B^(2q+1) Omega with B the affine map of
+ * RAFEAST_OPT_WARMSTART_MAP, Q = orth(Y), then Rayleigh-Ritz on A keeps the
+ * m0 Ritz vectors whose Ritz values are closest to (lmin+lmax)/2. The result
+ * becomes the handle's subspace (used by RAFEAST_START_SUBSPACE). */
+int rafeast_warmstart(rafeast_t h, double lmin, double lmax, int m0, int p,
+                      int q, uint64_t seed);
+
+/* Inject a subspace (the warm-start injection of Section 6; also a resume
+ * point): Q0 is n x m0 column-major, host or device per on_device; it is
+ * orthonormalised and Rayleigh-Ritz'ed into the handle. */
+int rafeast_set_subspace(rafeast_t h, const double* Q0, int m0, int on_device);
+
+/* Copy the handle's current subspace (n x m0) and its Ritz values (m0, host,
+ * may be NULL) out; Q host or device per on_device. -7 without one. */
+int rafeast_get_subspace(rafeast_t h, double* Q, double* theta, int m0,
+                         int on_device);
+
+/* FEAST / RA-FEAST Phase 2 (Algorithms 1 and 2): iterate filter, QR,
+ * Rayleigh-Ritz until every Ritz pair inside [lmin, lmax] has relative
+ * residual <= outer_tol or max_outer iterations ran. Outputs (host or device
+ * per outputs_on_device): evals[m0] Ritz values, the first *m_found of which
+ * lie inside the interval in ascending order; evecs[n*m0] the matching
+ * vectors, column-major; resid[m0] their relative residuals. m_found is a
+ * host int. Returns 0, or 1/2/3 with valid outputs (no eigenvalue inside, no
+ * convergence, m0 too small), or a negative error. The final subspace stays
+ * in the handle. */
+int rafeast_solve(rafeast_t h, const rafeast_params* prm, int* m_found,
+                  double* evals, double* evecs, double* resid,
+                  int outputs_on_device, rafeast_info* info);
+
+/* Solve count independent problems (handles, each with its own params and
+ * outputs, arrays of count pointers) with their COCG iterations batched into
+ * shared launches: one sparse-product launch per COCG step covers every
+ * instance. Outputs as rafeast_solve, per instance; statuses[count] receives
+ * each instance's status (host). Returns the first negative status, or 0. */
+int rafeast_solve_batched(int count, rafeast_t const* hs,
+                          const rafeast_params* prms, int* m_found,
+                          double* const* evals, double* const* evecs,
+                          double* const* resid, int outputs_on_device,
+                          rafeast_info* infos, int* statuses);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAFEAST_H */
