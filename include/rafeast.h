@@ -86,8 +86,8 @@ typedef struct rafeast_ctx* rafeast_t;
 /* Solver parameters (all host). Field order is part of the ABI. */
 typedef struct rafeast_params {
   double lmin, lmax;     /* search interval, lmin < lmax                      */
-  int32_t m0;            /* subspace size, 1..1024, >= eigenvalues inside     */
-  int32_t nc;            /* quadrature nodes on the half contour, 1..16        */
+  int32_t m0;            /* subspace size, 1..128, > eigenvalues inside       */
+  int32_t nc;            /* quadrature nodes on the half contour, 1..8         */
   double ellipse_ratio;  /* imaginary/real semi-axis ratio e, (0, 1]           */
   double solve_tol;      /* COCG: stop when ||r||_2 <= solve_tol * ||b||_2     */
   double outer_tol;      /* stop when max in-interval ||Av-lv||/||A||_1 <= tol */
@@ -141,6 +141,11 @@ void rafeast_destroy(rafeast_t h);
 
 /* Static English text for a status code. */
 const char* rafeast_status_string(int status);
+
+/* Text of the last CUDA failure seen by this thread (empty when none): the
+ * failing runtime call, its error string and source location. Valid until
+ * the next call on the same thread. */
+const char* rafeast_last_error(void);
 
 /* Set a tuning option (RAFEAST_OPT_*). -1 for an unknown key or value. */
 int rafeast_set_option(rafeast_t h, int key, int64_t value);

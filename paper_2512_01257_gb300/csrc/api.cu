@@ -1,0 +1,1158 @@
+// C-ABI of librafeast (declared in include/rafeast.h): handle lifecycle and
+// the FEAST / RA-FEAST driver. Every numerical step runs in the kernels of
+// kernels_sparse.cu / kernels_dense.cu on the handle's stream; the host only
+// sequences launches, reads back the m0 Ritz values and residuals once per
+// outer iteration, and takes the convergence decision (Algorithm 1's
+// "until convergence"). The COCG inner iterations are captured as CUDA
+// graphs of `chunk` steps and replayed until the device reports that every
+// system has converged.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace rafeast {
+
+static thread_local char g_err[512] = "";
+
+void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_err, sizeof(g_err), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+void* scratch(Handle* h, int slot, size_t bytes) {
+  if ((int)h->bufs.size() <= slot) h->bufs.resize(slot + 1);
+  DevBuf& b = h->bufs[slot];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes < bytes) {
+    if (b.p) RF_CUDA(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+    RF_CUDA(cudaMalloc(&b.p, bytes));
+    b.bytes = bytes;
+  }
+  return b.p;
+}
+
+static inline int even(int m) { return m + (m & 1); }
+
+struct CallScope {
+  Handle* h;
+  explicit CallScope(Handle* hh) : h(hh) {
+    h->launches = 0;
+    h->spmm_launches = 0;
+    RF_CUDA(cudaSetDevice(h->device));
+    RF_CUDA(cudaEventRecord(h->ev_in, h->user_stream));
+    RF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+  }
+  void finish() {
+    RF_CUDA(cudaEventRecord(h->ev_out, h->stream));
+    RF_CUDA(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// dense building blocks on internal row-major blocks
+// ---------------------------------------------------------------------------
+struct DenseWs {
+  double* G;      // m x m
+  double* R;      // m x m
+  double* Rinv;   // m x m
+  double* V;      // m x m
+  double* Vw;     // (m+1)^2
+  double* w;      // m
+  double* part;   // gram partials
+  int* status;    // 4 ints
+  double* small;  // m doubles
+};
+
+static DenseWs dense_ws(Handle* h, int m) {
+  const size_t mm = (size_t)(m + 1) * (m + 1);
+  const int parts = 2 * h->num_sms;
+  char* base = (char*)scratch(h, S_GRAM, sizeof(double) * (5 * mm + 2 * (m + 1) +
+                                                          (size_t)parts * m * m) + 64);
+  DenseWs d;
+  double* p = (double*)base;
+  d.G = p; p += mm;
+  d.R = p; p += mm;
+  d.Rinv = p; p += mm;
+  d.V = p; p += mm;
+  d.Vw = p; p += mm;
+  d.w = p; p += m + 1;
+  d.small = p; p += m + 1;
+  d.part = p;
+  d.status = (int*)scratch(h, S_SMALL, 64);
+  return d;
+}
+
+// X (n x m, ld) <- X R^{-1}; returns number of shifted passes; R_total (host,
+// m x m row-major upper) accumulates the factor if non-null.
+static int cholqr(Handle* h, double*& X, double*& tmp, int m, int ld, std::vector<double>* Rtot) {
+  DenseWs d = dense_ws(h, m);
+  int shifted = 0;
+  int passes = 2;
+  std::vector<double> Racc;
+  if (Rtot) {
+    Racc.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) Racc[i * m + i] = 1.0;
+  }
+  for (int pass = 0; pass < passes; ++pass) {
+    gram(X, X, h->n, m, ld, d.G, d.part, h->num_sms, h->stream);
+    chol_inv(d.G, m, h->n, d.R, d.Rinv, d.status, h->stream);
+    h->launches += 3;
+    int st = 0;
+    RF_CUDA(cudaMemcpyAsync(&st, d.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    if (st == 2) throw Err{RAFEAST_ERR_CHOLESKY};
+    if (st == 1) {
+      ++shifted;
+      if (passes < 4) ++passes;
+    }
+    tall_gemm(X, h->n, m, ld, d.Rinv, m, tmp, ld, h->stream);
+    h->launches += 1;
+    std::swap(X, tmp);
+    if (Rtot) {
+      std::vector<double> Rp((size_t)m * m), out((size_t)m * m, 0.0);
+      RF_CUDA(cudaMemcpyAsync(Rp.data(), d.R, sizeof(double) * m * m, cudaMemcpyDeviceToHost,
+                              h->stream));
+      RF_CUDA(cudaStreamSynchronize(h->stream));
+      // R_total <- R_pass * R_total
+      for (int i = 0; i < m; ++i)
+        for (int k = i; k < m; ++k) {
+          const double r = Rp[i * m + k];
+          if (r == 0.0) continue;
+          for (int j = 0; j < m; ++j) out[i * m + j] += r * Racc[k * m + j];
+        }
+      Racc.swap(out);
+    }
+  }
+  if (Rtot) *Rtot = Racc;
+  return shifted;
+}
+
+// Rayleigh-Ritz on X (n x m, ld, orthonormal): Qout = X V, AQout = (A X) V,
+// theta (device, m, ascending), resid2 (device, m).
+static void rayleigh_ritz_dev(Handle* h, const double* X, int m, int ld, double* Qout,
+                              double* AQout, double* theta_d, double* tmp) {
+  DenseWs d = dense_ws(h, m);
+  launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m, ld, 1.0, h->shift, X, tmp,
+                           h->num_sms, h->stream);
+  gram(X, tmp, h->n, m, ld, d.G, d.part, h->num_sms, h->stream);
+  jacobi_eigh(d.G, m, theta_d, d.V, d.Vw, h->stream);
+  tall_gemm(X, h->n, m, ld, d.V, m, Qout, ld, h->stream);
+  tall_gemm(tmp, h->n, m, ld, d.V, m, AQout, ld, h->stream);
+  h->launches += 7;
+  h->spmm_launches += 1;
+}
+
+static void residuals_host(Handle* h, const double* Q, const double* AQ, const double* theta_d,
+                           int m, int ld, std::vector<double>& res) {
+  DenseWs d = dense_ws(h, m);
+  col_resid2(Q, AQ, theta_d, h->n, m, ld, d.small, h->stream);
+  h->launches += 1;
+  res.resize(m);
+  RF_CUDA(cudaMemcpyAsync(res.data(), d.small, sizeof(double) * m, cudaMemcpyDeviceToHost,
+                          h->stream));
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < m; ++i) res[i] = std::sqrt(std::max(res[i], 0.0)) / h->norm1;
+}
+
+// ---------------------------------------------------------------------------
+// batched COCG filter: Qt = sum_j Re(w_j X_j), (z_j I - A) X_j = Q
+// ---------------------------------------------------------------------------
+struct FilterStats {
+  int iters_max = 0, iters_min = 0, breakdown = 0, capped = 0;
+};
+
+template <typename T>
+static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, const double* AQd,
+                       const double* theta_d, const std::vector<double>& theta, int m0, int ldq,
+                       double* Qt, FilterStats& fs) {
+  using C = c2<T>;
+  const int nc = prm.nc;
+  const int NC = nc_pad(nc);
+  const bool fp64 = sizeof(T) == 8;
+  std::vector<double> zr, zi, wr, wi;
+  quadrature_nodes(prm.lmin, prm.lmax, nc, prm.ellipse_ratio, zr, zi, wr, wi);
+  const int nsys = m0 * NC;
+  const bool corr = prm.solve_form == RAFEAST_FORM_CORRECTION;
+  // host-side small tables
+  std::vector<double2> coef(nsys);
+  std::vector<double> finit(m0, 0.0);
+  for (int i = 0; i < m0; ++i)
+    for (int j = 0; j < NC; ++j) {
+      double2 c = make_double2(0.0, 0.0);
+      if (j < nc) {
+        if (corr) {
+          // w_j / (z_j - theta_i)
+          const double dr = zr[j] - theta[i], di = zi[j];
+          const double den = dr * dr + di * di;
+          c = make_double2((wr[j] * dr + wi[j] * di) / den, (wi[j] * dr - wr[j] * di) / den);
+          finit[i] += c.x;
+        } else {
+          c = make_double2(wr[j], wi[j]);
+        }
+      }
+      coef[i * NC + j] = c;
+    }
+  std::vector<C> zs(NC);
+  for (int j = 0; j < NC; ++j) {
+    const int jj = j < nc ? j : 0;
+    zs[j].x = (T)(zr[jj] - h->shift);
+    zs[j].y = (T)zi[jj];
+  }
+  // device buffers
+  const int ldc = even(m0 * NC);
+  const size_t state_elems = (size_t)h->n * ldc * 2;
+  T* state = (T*)scratch(h, S_STATE, 4 * state_elems * sizeof(T));
+  const int ldd = m0;
+  T* dacc = (T*)scratch(h, S_DACC, (size_t)h->n * ldd * sizeof(T));
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    size_t o = off;
+    off += bytes;
+    return o;
+  };
+  const size_t o_acc = carve(sizeof(double) * 5 * nsys);
+  const size_t o_st = carve(sizeof(SysState) * nsys);
+  const size_t o_cf = carve(sizeof(Coef<T>) * nsys);
+  const size_t o_col = carve(sizeof(int) * m0);
+  const size_t o_ctl = carve(sizeof(CocgCtl));
+  const size_t o_zs = carve(sizeof(C) * NC);
+  const size_t o_coef = carve(sizeof(double2) * nsys);
+  const size_t o_fin = carve(sizeof(double) * m0);
+  char* sc = (char*)scratch(h, S_SCAL, off + 256);
+  RF_CUDA(cudaMemcpyAsync(sc + o_zs, zs.data(), sizeof(C) * NC, cudaMemcpyHostToDevice, h->stream));
+  RF_CUDA(cudaMemcpyAsync(sc + o_coef, coef.data(), sizeof(double2) * nsys, cudaMemcpyHostToDevice,
+                          h->stream));
+  RF_CUDA(cudaMemcpyAsync(sc + o_fin, finit.data(), sizeof(double) * m0, cudaMemcpyHostToDevice,
+                          h->stream));
+  CocgArgs<T> a;
+  a.n = h->n;
+  a.rowptr = h->rowptr;
+  a.colidx = h->colidx;
+  a.val = fp64 ? (const T*)h->val64 : (const T*)h->val32;
+  a.m0 = m0;
+  a.ldc = ldc;
+  int colblocks = 1;
+  choose_shape(m0, NC, fp64, h->opt_lanes, a.lanes, a.cpl, colblocks);
+  a.r[0] = state;
+  a.r[1] = state + state_elems;
+  a.p[0] = state + 2 * state_elems;
+  a.p[1] = state + 3 * state_elems;
+  a.dacc = dacc;
+  a.ldd = ldd;
+  a.qin = Qd;
+  a.aqin = AQd;
+  a.ldq = ldq;
+  a.theta = theta_d;
+  a.zs = sc + o_zs;
+  a.coef = (const double2*)(sc + o_coef);
+  a.acc = (double*)(sc + o_acc);
+  a.st = (SysState*)(sc + o_st);
+  a.cf = (Coef<T>*)(sc + o_cf);
+  a.colact = (int*)(sc + o_col);
+  a.ctl = (CocgCtl*)(sc + o_ctl);
+  a.nc_real = nc;
+  a.tol2 = prm.solve_tol * prm.solve_tol;
+  a.max_inner = prm.max_inner;
+  a.form = prm.solve_form;
+  launch_cocg_init<T>(a, NC, h->num_sms, h->stream);
+  h->launches += 2;
+  // capture `chunk` COCG steps as one graph
+  int chunk = std::max(2, h->opt_chunk);
+  chunk += chunk & 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  RF_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    for (int it = 0; it < chunk; ++it) {
+      launch_cocg_dots<T>(a, NC, it & 1, h->num_sms, h->stream);
+      launch_cocg_update<T>(a, NC, it & 1, h->num_sms, h->stream);
+    }
+  } catch (...) {
+    cudaStreamEndCapture(h->stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    throw;
+  }
+  RF_CUDA(cudaStreamEndCapture(h->stream, &graph));
+  RF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  CocgCtl ctl;
+  const int max_replays = (prm.max_inner + 2) / chunk + 2;
+  int replays = 0;
+  for (; replays < max_replays; ++replays) {
+    RF_CUDA(cudaGraphLaunch(exec, h->stream));
+    RF_CUDA(cudaMemcpyAsync(&ctl, a.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    if (ctl.done) break;
+  }
+  h->launches += 2 * chunk * (replays + 1);
+  h->spmm_launches += 2 * chunk * (replays + 1);
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (!ctl.done) throw Err{RAFEAST_ERR_TIMEOUT};
+  fs.iters_max = ctl.max_iters;
+  fs.iters_min = ctl.min_iters;
+  fs.breakdown = ctl.breakdown;
+  fs.capped = ctl.capped;
+  // Qt = f(theta) Q + D
+  launch_combine<T>(Qd, ldq, dacc, ldd, (const double*)(sc + o_fin), h->n, m0, Qt, h->stream);
+  h->launches += 1;
+  if (fs.breakdown) throw Err{RAFEAST_ERR_COCG_BREAKDOWN};
+}
+
+static void validate_params(const rafeast_params* p) {
+  RF_CHECK(p, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(std::isfinite(p->lmin) && std::isfinite(p->lmax) && p->lmin < p->lmax,
+           RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(p->m0 >= 1 && p->m0 <= 128, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(p->nc >= 1 && p->nc <= 8, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(p->ellipse_ratio > 0.0 && p->ellipse_ratio <= 1.0, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(p->solve_tol >= 0.0 && p->outer_tol >= 0.0, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(p->max_outer >= 1 && p->max_inner >= 1, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(p->precision == RAFEAST_FP64 || p->precision == RAFEAST_MIXED, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(p->solve_form == RAFEAST_FORM_DIRECT || p->solve_form == RAFEAST_FORM_CORRECTION,
+           RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(p->start == RAFEAST_START_RANDOM || p->start == RAFEAST_START_SUBSPACE,
+           RAFEAST_ERR_INVALID_ARG);
+}
+
+static void run_filter(Handle* h, const rafeast_params& prm, const double* Qd, const double* AQd,
+                       const double* theta_d, const std::vector<double>& theta, int m0, int ldq,
+                       double* Qt, FilterStats& fs) {
+  if (prm.precision == RAFEAST_FP64)
+    filter_dev<double>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, Qt, fs);
+  else
+    filter_dev<float>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, Qt, fs);
+}
+
+// column-major caller block (host or device) -> internal row-major device
+static void import_block(Handle* h, const double* src, int m, int on_device, double* dst, int ld) {
+  const double* dsrc = src;
+  if (!on_device) {
+    double* tmp = (double*)scratch(h, S_IO1, sizeof(double) * h->n * m);
+    RF_CUDA(cudaMemcpyAsync(tmp, src, sizeof(double) * h->n * m, cudaMemcpyHostToDevice, h->stream));
+    dsrc = tmp;
+  }
+  launch_to_internal(h->n, m, dsrc, dst, ld, h->perm, h->stream);
+  h->launches += 1;
+}
+
+static void export_block(Handle* h, const double* src, int ld, int m, const int32_t* cols_d,
+                         int on_device, double* dst) {
+  if (m <= 0) return;
+  double* ddst = dst;
+  if (!on_device) ddst = (double*)scratch(h, S_IO2, sizeof(double) * h->n * m);
+  launch_from_internal(h->n, m, src, ld, ddst, h->perm, cols_d, h->stream);
+  h->launches += 1;
+  if (!on_device) {
+    RF_CUDA(cudaMemcpyAsync(dst, ddst, sizeof(double) * h->n * m, cudaMemcpyDeviceToHost,
+                            h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+  }
+}
+
+static void ensure_subspace_bufs(Handle* h, int m0) {
+  const int ldq = even(m0);
+  if (h->m0 != m0 || !h->Q) {
+    if (h->Q) cudaFree(h->Q);
+    if (h->AQ) cudaFree(h->AQ);
+    if (h->theta_d) cudaFree(h->theta_d);
+    h->Q = h->AQ = h->theta_d = nullptr;
+    h->m0 = 0;
+    RF_CUDA(cudaMalloc(&h->Q, sizeof(double) * h->n * ldq));
+    RF_CUDA(cudaMalloc(&h->AQ, sizeof(double) * h->n * ldq));
+    RF_CUDA(cudaMalloc(&h->theta_d, sizeof(double) * (m0 + 1)));
+    RF_CUDA(cudaMemsetAsync(h->Q, 0, sizeof(double) * h->n * ldq, h->stream));
+    RF_CUDA(cudaMemsetAsync(h->AQ, 0, sizeof(double) * h->n * ldq, h->stream));
+    h->ldq = ldq;
+  }
+}
+
+// orthonormalise + Rayleigh-Ritz a block already in h->Q (m0 columns)
+static void subspace_from_Q(Handle* h, int m0) {
+  const int ldq = h->ldq;
+  double* tmp = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ldq);
+  double* X = h->Q;
+  double* Y = tmp;
+  cholqr(h, X, Y, m0, ldq, nullptr);
+  double* tmp2 = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ldq);
+  // X holds the orthonormal block (either h->Q or tmp)
+  double* Qout = (X == h->Q) ? tmp : h->Q;
+  rayleigh_ritz_dev(h, X, m0, ldq, Qout, h->AQ, h->theta_d, tmp2);
+  if (Qout != h->Q)
+    RF_CUDA(cudaMemcpyAsync(h->Q, Qout, sizeof(double) * h->n * ldq, cudaMemcpyDeviceToDevice,
+                            h->stream));
+  h->theta.resize(m0);
+  RF_CUDA(cudaMemcpyAsync(h->theta.data(), h->theta_d, sizeof(double) * m0,
+                          cudaMemcpyDeviceToHost, h->stream));
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  h->m0 = m0;
+}
+
+}  // namespace rafeast
+
+using namespace rafeast;
+
+#define API_BEGIN try {
+#define API_END                              \
+  }                                          \
+  catch (const Err& e) {                     \
+    return e.code;                           \
+  }                                          \
+  catch (...) {                              \
+    return RAFEAST_ERR_CUDA;                 \
+  }
+
+extern "C" {
+
+const char* rafeast_status_string(int s) {
+  switch (s) {
+    case RAFEAST_OK: return "ok";
+    case RAFEAST_NO_EIGENVALUE: return "no eigenvalue inside the interval";
+    case RAFEAST_NO_CONVERGENCE: return "no convergence within max_outer iterations";
+    case RAFEAST_M0_TOO_SMALL: return "m0 too small: every Ritz value lies inside the interval";
+    case RAFEAST_ERR_INVALID_ARG: return "invalid argument";
+    case RAFEAST_ERR_NOT_SYMMETRIC: return "matrix is not symmetric";
+    case RAFEAST_ERR_CUDA: return "CUDA error";
+    case RAFEAST_ERR_COCG_BREAKDOWN: return "COCG breakdown";
+    case RAFEAST_ERR_TIMEOUT: return "device work did not finish within its bound";
+    case RAFEAST_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case RAFEAST_ERR_NOT_READY: return "no subspace in the handle";
+    case RAFEAST_ERR_CHOLESKY: return "Cholesky-QR failed (rank-deficient block)";
+    case RAFEAST_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown status";
+  }
+}
+
+const char* rafeast_last_error(void) { return g_err; }
+
+int rafeast_quadrature(double lmin, double lmax, int nc, double e, double* z, double* w) {
+  if (!z || !w || !(lmin < lmax) || nc < 1 || nc > 64 || !(e > 0.0 && e <= 1.0))
+    return RAFEAST_ERR_INVALID_ARG;
+  std::vector<double> zr, zi, wr, wi;
+  quadrature_nodes(lmin, lmax, nc, e, zr, zi, wr, wi);
+  for (int j = 0; j < nc; ++j) {
+    z[2 * j] = zr[j];
+    z[2 * j + 1] = zi[j];
+    w[2 * j] = wr[j];
+    w[2 * j + 1] = wi[j];
+  }
+  return RAFEAST_OK;
+}
+
+int rafeast_philox(uint64_t seed, uint64_t first_block, int64_t nblocks, uint64_t* words,
+                   void* stream) {
+  API_BEGIN
+  if (nblocks < 0 || (nblocks > 0 && !words)) return RAFEAST_ERR_INVALID_ARG;
+  launch_philox(seed, first_block, nblocks, words, (cudaStream_t)stream);
+  RF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return RAFEAST_OK;
+  API_END
+}
+
+int rafeast_create(rafeast_t* out, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                   const int32_t* col_idx, const double* values, double diag_shift,
+                   int inputs_on_device, void* stream, uint32_t flags) {
+  if (!out) return RAFEAST_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n <= 0 || nnz < 0 || n > INT32_MAX - 1 || nnz > INT32_MAX || !row_ptr ||
+      (nnz > 0 && (!col_idx || !values)) || !std::isfinite(diag_shift))
+    return RAFEAST_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return RAFEAST_ERR_NO_DEVICE;
+  Handle* h = new Handle();
+  try {
+    RF_CUDA(cudaGetDevice(&h->device));
+    RF_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->n = n;
+    h->nnz = nnz;
+    h->shift = diag_shift;
+    h->user_stream = (cudaStream_t)stream;
+    RF_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    RF_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    RF_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    CallScope scope(h);
+    // host copies for validation and reordering
+    std::vector<int32_t> rp(n + 1), ci(nnz);
+    std::vector<double> va(nnz);
+    auto kind = inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    RF_CUDA(cudaMemcpy(rp.data(), row_ptr, sizeof(int32_t) * (n + 1), kind));
+    if (nnz) {
+      RF_CUDA(cudaMemcpy(ci.data(), col_idx, sizeof(int32_t) * nnz, kind));
+      RF_CUDA(cudaMemcpy(va.data(), values, sizeof(double) * nnz, kind));
+    }
+    RF_CHECK(rp[0] == 0 && rp[n] == nnz, RAFEAST_ERR_INVALID_ARG);
+    for (int64_t i = 0; i < n; ++i) RF_CHECK(rp[i + 1] >= rp[i], RAFEAST_ERR_INVALID_ARG);
+    for (int64_t k = 0; k < nnz; ++k)
+      RF_CHECK(ci[k] >= 0 && ci[k] < n && std::isfinite(va[k]), RAFEAST_ERR_INVALID_ARG);
+    if (flags & RAFEAST_CREATE_CHECK_SYMMETRY) {
+      // every (i, j, v) needs a matching (j, i, v)
+      std::vector<std::pair<int32_t, double>> rowv;
+      for (int64_t i = 0; i < n; ++i)
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+          const int32_t j = ci[k];
+          bool found = false;
+          for (int32_t t = rp[j]; t < rp[j + 1]; ++t)
+            if (ci[t] == i && va[t] == va[k]) {
+              found = true;
+              break;
+            }
+          if (!found) throw Err{RAFEAST_ERR_NOT_SYMMETRIC};
+        }
+    }
+    // norms: ||A||_1 and Gershgorin interval of A = L + shift I
+    double norm1 = 0.0, glo = INFINITY, ghi = -INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+      double d = diag_shift, off = 0.0;
+      for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        if (ci[k] == i) d += va[k];
+        else off += std::fabs(va[k]);
+      }
+      norm1 = std::max(norm1, off + std::fabs(d));
+      glo = std::min(glo, d - off);
+      ghi = std::max(ghi, d + off);
+    }
+    h->norm1 = norm1 > 0.0 ? norm1 : 1.0;
+    h->glo = glo;
+    h->ghi = ghi;
+    // row order: reverse Cuthill-McKee when it narrows the band
+    std::vector<int32_t> perm;
+    bool reorder = false;
+    if (!(flags & RAFEAST_CREATE_NO_REORDER) && n > 1) {
+      rcm_order(n, rp.data(), ci.data(), perm);
+      const int64_t bw0 = bandwidth(n, rp.data(), ci.data(), nullptr);
+      const int64_t bw1 = bandwidth(n, rp.data(), ci.data(), perm.data());
+      reorder = (flags & RAFEAST_CREATE_FORCE_REORDER) || (double)bw1 < 0.7 * (double)bw0;
+    }
+    std::vector<int32_t> rp2 = rp, ci2 = ci;
+    std::vector<double> va2 = va;
+    if (reorder) {
+      std::vector<int32_t> ip(n);
+      for (int64_t r = 0; r < n; ++r) ip[perm[r]] = (int32_t)r;
+      rp2[0] = 0;
+      for (int64_t r = 0; r < n; ++r) rp2[r + 1] = rp2[r] + (rp[perm[r] + 1] - rp[perm[r]]);
+      std::vector<std::pair<int32_t, double>> row;
+      for (int64_t r = 0; r < n; ++r) {
+        const int32_t o = perm[r];
+        row.clear();
+        for (int32_t k = rp[o]; k < rp[o + 1]; ++k) row.emplace_back(ip[ci[k]], va[k]);
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                    return a.first < b.first;
+                  });
+        for (size_t t = 0; t < row.size(); ++t) {
+          ci2[rp2[r] + t] = row[t].first;
+          va2[rp2[r] + t] = row[t].second;
+        }
+      }
+      RF_CUDA(cudaMalloc(&h->perm, sizeof(int32_t) * n));
+      RF_CUDA(cudaMalloc(&h->iperm, sizeof(int32_t) * n));
+      RF_CUDA(cudaMemcpy(h->perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+      RF_CUDA(cudaMemcpy(h->iperm, ip.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    }
+    h->reordered = reorder;
+    std::vector<float> v32(nnz);
+    for (int64_t k = 0; k < nnz; ++k) v32[k] = (float)va2[k];
+    RF_CUDA(cudaMalloc(&h->rowptr, sizeof(int32_t) * (n + 1)));
+    RF_CUDA(cudaMalloc(&h->colidx, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    RF_CUDA(cudaMalloc(&h->val64, sizeof(double) * std::max<int64_t>(nnz, 1)));
+    RF_CUDA(cudaMalloc(&h->val32, sizeof(float) * std::max<int64_t>(nnz, 1)));
+    RF_CUDA(cudaMemcpy(h->rowptr, rp2.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+    if (nnz) {
+      RF_CUDA(cudaMemcpy(h->colidx, ci2.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+      RF_CUDA(cudaMemcpy(h->val64, va2.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+      RF_CUDA(cudaMemcpy(h->val32, v32.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
+    }
+    scope.finish();
+    *out = reinterpret_cast<rafeast_t>(h);
+    return RAFEAST_OK;
+  } catch (const Err& e) {
+    rafeast_destroy(reinterpret_cast<rafeast_t>(h));
+    return e.code;
+  } catch (...) {
+    rafeast_destroy(reinterpret_cast<rafeast_t>(h));
+    return RAFEAST_ERR_CUDA;
+  }
+}
+
+void rafeast_destroy(rafeast_t hh) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& b : h->bufs)
+    if (b.p) cudaFree(b.p);
+  void* ptrs[] = {h->rowptr, h->colidx, h->val64, h->val32, h->perm, h->iperm,
+                  h->Q,      h->AQ,     h->theta_d};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return RAFEAST_ERR_INVALID_ARG;
+  switch (key) {
+    case RAFEAST_OPT_WARMSTART_MAP:
+      if (value < 0 || value > 2) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_ws_map = (int)value;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_CHUNK:
+      if (value < 2 || value > 512) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_chunk = (int)value;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_AUTOTUNE:
+      h->opt_autotune = value ? 1 : 0;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_LANES:
+      if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32)
+        return RAFEAST_ERR_INVALID_ARG;
+      h->opt_lanes = (int)value;
+      return RAFEAST_OK;
+    default:
+      return RAFEAST_ERR_INVALID_ARG;
+  }
+}
+
+int rafeast_matrix_info(rafeast_t hh, int64_t* n, int* reordered, double* norm1, double* glo,
+                        double* ghi) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return RAFEAST_ERR_INVALID_ARG;
+  if (n) *n = h->n;
+  if (reordered) *reordered = h->reordered ? 1 : 0;
+  if (norm1) *norm1 = h->norm1;
+  if (glo) *glo = h->glo;
+  if (ghi) *ghi = h->ghi;
+  return RAFEAST_OK;
+}
+
+int rafeast_draw_omega(rafeast_t hh, uint64_t seed, int k, double* omega) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || k < 1 || !omega) return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  CallScope scope(h);
+  launch_omega(seed, h->n, k, omega, h->stream);
+  scope.finish();
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  return RAFEAST_OK;
+  API_END
+}
+
+int rafeast_spmm(rafeast_t hh, int k, double alpha, double beta, const double* X, double* Y,
+                 int precision) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || k < 1 || !X || !Y || (precision != RAFEAST_FP64 && precision != RAFEAST_MIXED))
+    return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  CallScope scope(h);
+  const int ld = even(k);
+  double* Xi = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ld);
+  double* Yi = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ld);
+  launch_to_internal(h->n, k, X, Xi, ld, h->perm, h->stream);
+  // Y = alpha (L + shift I) X + beta X = alpha L X + (alpha shift + beta) X
+  if (precision == RAFEAST_FP64) {
+    launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, k, ld, alpha,
+                             alpha * h->shift + beta, Xi, Yi, h->num_sms, h->stream);
+  } else {
+    float* Xf = (float*)scratch(h, S_AQ2, sizeof(float) * h->n * ld * 2);
+    float* Yf = Xf + h->n * ld;
+    launch_cast_to_f32(Xi, Xf, h->n * (int64_t)ld, h->stream);
+    launch_spmm_real<float>(h->n, h->rowptr, h->colidx, h->val32, k, ld, alpha,
+                            alpha * h->shift + beta, Xf, Yf, h->num_sms, h->stream);
+    launch_widen(Yf, Yi, h->n * (int64_t)ld, h->stream);
+  }
+  launch_from_internal(h->n, k, Yi, ld, Y, h->perm, nullptr, h->stream);
+  scope.finish();
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  return RAFEAST_OK;
+  API_END
+}
+
+int rafeast_shifted_spmm(rafeast_t hh, int nc, const double* z, int m, const double* P, double* W,
+                         int precision) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || nc < 1 || nc > 8 || m < 1 || !z || !P || !W ||
+      (precision != RAFEAST_FP64 && precision != RAFEAST_MIXED))
+    return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  CallScope scope(h);
+  const int NC = nc_pad(nc);
+  const int ldc = even(m * NC);
+  const bool fp64 = precision == RAFEAST_FP64;
+  // caller layout: entry (i, col, j) at 2*((col*nc + j)*n + i); internal:
+  // row r, column col, shift j at 2*(r*ldc + col*NC + j). Move through a
+  // real-valued internal block of 2*m*NC columns.
+  const int kre = 2 * m * nc;
+  const int ldr = even(kre);
+  double* tin = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * std::max(ldr, 2 * ldc));
+  double* tout = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * std::max(ldr, 2 * ldc));
+  // caller array viewed as column-major n x kre with column index 2*(col*nc+j)+{0,1}?
+  // No: caller stores (re, im) pairs contiguously per row entry, so view it as
+  // column-major (2n) x (m*nc) and reorganise on the host side of the copy.
+  std::vector<double> hp((size_t)2 * h->n * m * nc);
+  RF_CUDA(cudaMemcpy(hp.data(), P, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost));
+  std::vector<int32_t> pm(h->n);
+  if (h->perm) RF_CUDA(cudaMemcpy(pm.data(), h->perm, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost));
+  else std::iota(pm.begin(), pm.end(), 0);
+  std::vector<double> hin((size_t)h->n * ldc * 2, 0.0);
+  for (int64_t r = 0; r < h->n; ++r)
+    for (int col = 0; col < m; ++col)
+      for (int j = 0; j < nc; ++j) {
+        const size_t src = 2 * (((size_t)col * nc + j) * h->n + pm[r]);
+        const size_t dst = 2 * ((size_t)r * ldc + (size_t)col * NC + j);
+        hin[dst] = hp[src];
+        hin[dst + 1] = hp[src + 1];
+      }
+  std::vector<double> hz(2 * NC);
+  for (int j = 0; j < NC; ++j) {
+    const int jj = j < nc ? j : 0;
+    hz[2 * j] = z[2 * jj] - h->shift;
+    hz[2 * j + 1] = z[2 * jj + 1];
+  }
+  int lanes, cpl, cb;
+  choose_shape(m, NC, fp64, h->opt_lanes, lanes, cpl, cb);
+  std::vector<double> hout(hin.size());
+  if (fp64) {
+    double* zs = (double*)scratch(h, S_SMALL, sizeof(double) * 2 * NC + 64);
+    RF_CUDA(cudaMemcpy(tin, hin.data(), sizeof(double) * hin.size(), cudaMemcpyHostToDevice));
+    RF_CUDA(cudaMemcpy(zs, hz.data(), sizeof(double) * 2 * NC, cudaMemcpyHostToDevice));
+    launch_shifted_spmm<double>(h->n, h->rowptr, h->colidx, h->val64, m, ldc, NC, zs, tin, tout,
+                                lanes, cpl, h->num_sms, h->stream);
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    RF_CUDA(cudaMemcpy(hout.data(), tout, sizeof(double) * hout.size(), cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> fin(hin.size()), fout(hin.size());
+    for (size_t t = 0; t < hin.size(); ++t) fin[t] = (float)hin[t];
+    std::vector<float> fz(2 * NC);
+    for (int t = 0; t < 2 * NC; ++t) fz[t] = (float)hz[t];
+    float* zs = (float*)scratch(h, S_SMALL, sizeof(float) * 2 * NC + 64);
+    float* fi = (float*)tin;
+    float* fo = (float*)tout;
+    RF_CUDA(cudaMemcpy(fi, fin.data(), sizeof(float) * fin.size(), cudaMemcpyHostToDevice));
+    RF_CUDA(cudaMemcpy(zs, fz.data(), sizeof(float) * 2 * NC, cudaMemcpyHostToDevice));
+    launch_shifted_spmm<float>(h->n, h->rowptr, h->colidx, h->val32, m, ldc, NC, zs, fi, fo,
+                               lanes, cpl, h->num_sms, h->stream);
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    RF_CUDA(cudaMemcpy(fout.data(), fo, sizeof(float) * fout.size(), cudaMemcpyDeviceToHost));
+    for (size_t t = 0; t < hout.size(); ++t) hout[t] = fout[t];
+  }
+  std::vector<double> hw(hp.size());
+  for (int64_t r = 0; r < h->n; ++r)
+    for (int col = 0; col < m; ++col)
+      for (int j = 0; j < nc; ++j) {
+        const size_t dst = 2 * (((size_t)col * nc + j) * h->n + pm[r]);
+        const size_t src = 2 * ((size_t)r * ldc + (size_t)col * NC + j);
+        hw[dst] = hout[src];
+        hw[dst + 1] = hout[src + 1];
+      }
+  RF_CUDA(cudaMemcpy(W, hw.data(), sizeof(double) * hw.size(), cudaMemcpyHostToDevice));
+  scope.finish();
+  return RAFEAST_OK;
+  API_END
+}
+
+int rafeast_filter(rafeast_t hh, const rafeast_params* prm, const double* Q, const double* theta,
+                   double* Qt, rafeast_info* info) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !Q || !Qt) return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  validate_params(prm);
+  CallScope scope(h);
+  const int m0 = prm->m0, ldq = even(m0);
+  double* Qi = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ldq);
+  double* AQi = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ldq);
+  double* Qti = (double*)scratch(h, S_QT, sizeof(double) * h->n * ldq);
+  RF_CUDA(cudaMemsetAsync(Qti, 0, sizeof(double) * h->n * ldq, h->stream));
+  launch_to_internal(h->n, m0, Q, Qi, ldq, h->perm, h->stream);
+  launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m0, ldq, 1.0, h->shift, Qi, AQi,
+                           h->num_sms, h->stream);
+  std::vector<double> th(m0);
+  double* th_d = (double*)scratch(h, S_OMEGA, sizeof(double) * (m0 + 1));
+  if (theta) {
+    th.assign(theta, theta + m0);
+  } else {
+    // Rayleigh quotients q_i^T A q_i / q_i^T q_i
+    std::vector<double> num(m0), den(m0);
+    DenseWs d = dense_ws(h, m0);
+    col_dot(Qi, AQi, h->n, m0, ldq, d.small, h->stream);
+    RF_CUDA(cudaMemcpyAsync(num.data(), d.small, sizeof(double) * m0, cudaMemcpyDeviceToHost,
+                            h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    col_dot(Qi, Qi, h->n, m0, ldq, d.small, h->stream);
+    RF_CUDA(cudaMemcpyAsync(den.data(), d.small, sizeof(double) * m0, cudaMemcpyDeviceToHost,
+                            h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < m0; ++i) th[i] = den[i] > 0 ? num[i] / den[i] : 0.0;
+  }
+  RF_CUDA(cudaMemcpyAsync(th_d, th.data(), sizeof(double) * m0, cudaMemcpyHostToDevice, h->stream));
+  FilterStats fs;
+  cudaEvent_t e0, e1;
+  RF_CUDA(cudaEventCreate(&e0));
+  RF_CUDA(cudaEventCreate(&e1));
+  RF_CUDA(cudaEventRecord(e0, h->stream));
+  int rc = RAFEAST_OK;
+  try {
+    run_filter(h, *prm, Qi, AQi, th_d, th, m0, ldq, Qti, fs);
+  } catch (const Err& e) {
+    rc = e.code;
+  }
+  RF_CUDA(cudaEventRecord(e1, h->stream));
+  launch_from_internal(h->n, m0, Qti, ldq, Qt, h->perm, nullptr, h->stream);
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = rc;
+    info->cocg_max_last = fs.iters_max;
+    info->cocg_min_last = fs.iters_min;
+    info->cocg_iters_total = fs.iters_max;
+    info->t_filter_ms = ms;
+    info->t_total_ms = ms;
+    info->kernel_launches = h->launches;
+    info->spmm_launches = h->spmm_launches;
+  }
+  scope.finish();
+  return rc;
+  API_END
+}
+
+int rafeast_orthonormalize(rafeast_t hh, int m, double* Q, double* R) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || m < 1 || m > 128 || !Q) return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  CallScope scope(h);
+  const int ld = even(m);
+  double* A = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ld);
+  double* B = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ld);
+  launch_to_internal(h->n, m, Q, A, ld, h->perm, h->stream);
+  std::vector<double> Rt;
+  double* X = A;
+  double* Y = B;
+  cholqr(h, X, Y, m, ld, R ? &Rt : nullptr);
+  launch_from_internal(h->n, m, X, ld, Q, h->perm, nullptr, h->stream);
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  if (R) {
+    // column-major output of the row-major upper factor
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) R[(size_t)j * m + i] = Rt[(size_t)i * m + j];
+  }
+  scope.finish();
+  return RAFEAST_OK;
+  API_END
+}
+
+int rafeast_rayleigh_ritz(rafeast_t hh, int m, double* Q, double* theta, double* resid) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || m < 1 || m > 128 || !Q || !theta) return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  CallScope scope(h);
+  const int ld = even(m);
+  double* X = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ld);
+  double* tmp = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ld);
+  double* Qo = (double*)scratch(h, S_QT, sizeof(double) * h->n * ld);
+  double* AQo = (double*)scratch(h, S_AQ2, sizeof(double) * h->n * ld);
+  double* th_d = (double*)scratch(h, S_OMEGA, sizeof(double) * (m + 1));
+  launch_to_internal(h->n, m, Q, X, ld, h->perm, h->stream);
+  rayleigh_ritz_dev(h, X, m, ld, Qo, AQo, th_d, tmp);
+  std::vector<double> res;
+  residuals_host(h, Qo, AQo, th_d, m, ld, res);
+  RF_CUDA(cudaMemcpyAsync(theta, th_d, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+  launch_from_internal(h->n, m, Qo, ld, Q, h->perm, nullptr, h->stream);
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  if (resid) std::copy(res.begin(), res.end(), resid);
+  scope.finish();
+  return RAFEAST_OK;
+  API_END
+}
+
+int rafeast_warmstart(rafeast_t hh, double lmin, double lmax, int m0, int p, int q,
+                      uint64_t seed) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !(lmin < lmax) || m0 < 1 || p < 0 || q < 0 || m0 + p > 128 || m0 > 128 ||
+      m0 + p > h->n)
+    return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  CallScope scope(h);
+  const int k = m0 + p, ld = even(k);
+  // B = s A + t I (Algorithm 2 Phase 1; the low-end map for low intervals)
+  int which = h->opt_ws_map;
+  if (which == 0) which = (0.5 * (lmin + lmax) >= 0.5 * (h->glo + h->ghi)) ? 1 : 2;
+  double s, t;
+  if (which == 1) {
+    s = 1.0 / (lmax - lmin);
+    t = -lmin * s;
+  } else {
+    s = -1.0 / (h->ghi - lmin);
+    t = h->ghi / (h->ghi - lmin);
+  }
+  const double sL = s, sI = s * h->shift + t;  // B X = s L X + (s shift + t) X
+  double* om = (double*)scratch(h, S_OMEGA, sizeof(double) * h->n * k);
+  double* Y = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ld);
+  double* Z = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ld);
+  launch_omega(seed, h->n, k, om, h->stream);
+  launch_to_internal(h->n, k, om, Z, ld, h->perm, h->stream);
+  launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, k, ld, sL, sI, Z, Y, h->num_sms,
+                           h->stream);
+  h->launches += 3;
+  h->spmm_launches += 1;
+  for (int it = 0; it < q; ++it) {
+    cholqr(h, Y, Z, k, ld, nullptr);
+    launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, k, ld, sL, sI, Y, Z,
+                             h->num_sms, h->stream);
+    launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, k, ld, sL, sI, Z, Y,
+                             h->num_sms, h->stream);
+    h->launches += 2;
+    h->spmm_launches += 2;
+  }
+  cholqr(h, Y, Z, k, ld, nullptr);
+  // Rayleigh-Ritz on the m0+p columns
+  double* Qall = (double*)scratch(h, S_QT, sizeof(double) * h->n * ld);
+  double* AQall = (double*)scratch(h, S_AQ2, sizeof(double) * h->n * ld);
+  double* th_all = (double*)scratch(h, S_IO1, sizeof(double) * (k + 1));
+  rayleigh_ritz_dev(h, Y, k, ld, Qall, AQall, th_all, Z);
+  std::vector<double> th(k);
+  RF_CUDA(cudaMemcpyAsync(th.data(), th_all, sizeof(double) * k, cudaMemcpyDeviceToHost,
+                          h->stream));
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  // keep the m0 Ritz values closest to the interval centre (stable ties)
+  const double c = 0.5 * (lmin + lmax);
+  std::vector<int> idx(k);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(),
+                   [&](int a, int b) { return std::fabs(th[a] - c) < std::fabs(th[b] - c); });
+  idx.resize(m0);
+  std::sort(idx.begin(), idx.end());
+  // selection matrix (k x m0) applied with the tall GEMM
+  std::vector<double> S((size_t)k * m0, 0.0);
+  for (int j = 0; j < m0; ++j) S[(size_t)idx[j] * m0 + j] = 1.0;
+  ensure_subspace_bufs(h, m0);
+  DenseWs d = dense_ws(h, k);
+  RF_CUDA(cudaMemcpyAsync(d.V, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice,
+                          h->stream));
+  RF_CUDA(cudaMemsetAsync(h->Q, 0, sizeof(double) * h->n * h->ldq, h->stream));
+  RF_CUDA(cudaMemsetAsync(h->AQ, 0, sizeof(double) * h->n * h->ldq, h->stream));
+  tall_gemm(Qall, h->n, k, ld, d.V, m0, h->Q, h->ldq, h->stream);
+  tall_gemm(AQall, h->n, k, ld, d.V, m0, h->AQ, h->ldq, h->stream);
+  h->theta.resize(m0);
+  for (int j = 0; j < m0; ++j) h->theta[j] = th[idx[j]];
+  RF_CUDA(cudaMemcpyAsync(h->theta_d, h->theta.data(), sizeof(double) * m0,
+                          cudaMemcpyHostToDevice, h->stream));
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  h->m0 = m0;
+  scope.finish();
+  return RAFEAST_OK;
+  API_END
+}
+
+int rafeast_set_subspace(rafeast_t hh, const double* Q0, int m0, int on_device) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !Q0 || m0 < 1 || m0 > 128 || m0 > h->n) return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  CallScope scope(h);
+  ensure_subspace_bufs(h, m0);
+  import_block(h, Q0, m0, on_device, h->Q, h->ldq);
+  subspace_from_Q(h, m0);
+  scope.finish();
+  return RAFEAST_OK;
+  API_END
+}
+
+int rafeast_get_subspace(rafeast_t hh, double* Q, double* theta, int m0, int on_device) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !Q) return RAFEAST_ERR_INVALID_ARG;
+  if (!h->Q || h->m0 == 0) return RAFEAST_ERR_NOT_READY;
+  if (m0 != h->m0) return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  CallScope scope(h);
+  export_block(h, h->Q, h->ldq, m0, nullptr, on_device, Q);
+  if (theta) std::copy(h->theta.begin(), h->theta.end(), theta);
+  scope.finish();
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  return RAFEAST_OK;
+  API_END
+}
+
+int rafeast_solve(rafeast_t hh, const rafeast_params* prm, int* m_found, double* evals,
+                  double* evecs, double* resid, int outputs_on_device, rafeast_info* info) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !m_found || !evals) return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  validate_params(prm);
+  RF_CHECK(prm->reserved == 0, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(prm->m0 <= h->n, RAFEAST_ERR_INVALID_ARG);
+  CallScope scope(h);
+  const int m0 = prm->m0;
+  cudaEvent_t ev[6];
+  for (auto& e : ev) RF_CUDA(cudaEventCreate(&e));
+  RF_CUDA(cudaEventRecord(ev[0], h->stream));
+  if (prm->start == RAFEAST_START_RANDOM) {
+    ensure_subspace_bufs(h, m0);
+    double* om = (double*)scratch(h, S_OMEGA, sizeof(double) * h->n * m0);
+    launch_omega(prm->seed, h->n, m0, om, h->stream);
+    launch_to_internal(h->n, m0, om, h->Q, h->ldq, h->perm, h->stream);
+    h->launches += 2;
+    double* X = h->Q;
+    double* Y = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * h->ldq);
+    cholqr(h, X, Y, m0, h->ldq, nullptr);
+    if (X != h->Q)
+      RF_CUDA(cudaMemcpyAsync(h->Q, X, sizeof(double) * h->n * h->ldq, cudaMemcpyDeviceToDevice,
+                              h->stream));
+    // A Q and Rayleigh quotients (the correction form's theta)
+    launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m0, h->ldq, 1.0, h->shift, h->Q,
+                             h->AQ, h->num_sms, h->stream);
+    h->launches += 1;
+    h->spmm_launches += 1;
+    DenseWs d = dense_ws(h, m0);
+    col_dot(h->Q, h->AQ, h->n, m0, h->ldq, h->theta_d, h->stream);
+    h->theta.resize(m0);
+    RF_CUDA(cudaMemcpyAsync(h->theta.data(), h->theta_d, sizeof(double) * m0,
+                            cudaMemcpyDeviceToHost, h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    (void)d;
+    h->m0 = m0;
+  } else {
+    if (!h->Q || h->m0 != m0) throw Err{RAFEAST_ERR_NOT_READY};
+  }
+  RF_CUDA(cudaEventRecord(ev[1], h->stream));
+  const int ldq = h->ldq;
+  double* Qt = (double*)scratch(h, S_QT, sizeof(double) * h->n * ldq);
+  double* T1 = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ldq);
+  double* T2 = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ldq);
+  RF_CUDA(cudaMemsetAsync(Qt, 0, sizeof(double) * h->n * ldq, h->stream));
+  RF_CUDA(cudaMemsetAsync(T1, 0, sizeof(double) * h->n * ldq, h->stream));
+  std::vector<double> res(m0, 0.0);
+  int status = RAFEAST_NO_CONVERGENCE;
+  int it = 0;
+  int cocg_total = 0;
+  FilterStats fs;
+  float t_filter = 0, t_orth = 0, t_rr = 0;
+  int shifted_total = 0;
+  for (it = 1; it <= prm->max_outer; ++it) {
+    RF_CUDA(cudaEventRecord(ev[2], h->stream));
+    run_filter(h, *prm, h->Q, h->AQ, h->theta_d, h->theta, m0, ldq, Qt, fs);
+    cocg_total += fs.iters_max;
+    RF_CUDA(cudaEventRecord(ev[3], h->stream));
+    double* X = Qt;
+    double* Y = T1;
+    shifted_total += cholqr(h, X, Y, m0, ldq, nullptr);
+    RF_CUDA(cudaEventRecord(ev[4], h->stream));
+    rayleigh_ritz_dev(h, X, m0, ldq, h->Q, h->AQ, h->theta_d, T2);
+    residuals_host(h, h->Q, h->AQ, h->theta_d, m0, ldq, res);
+    RF_CUDA(cudaEventRecord(ev[5], h->stream));
+    h->theta.resize(m0);
+    RF_CUDA(cudaMemcpyAsync(h->theta.data(), h->theta_d, sizeof(double) * m0,
+                            cudaMemcpyDeviceToHost, h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    float a = 0, b = 0, c = 0;
+    cudaEventElapsedTime(&a, ev[2], ev[3]);
+    cudaEventElapsedTime(&b, ev[3], ev[4]);
+    cudaEventElapsedTime(&c, ev[4], ev[5]);
+    t_filter += a;
+    t_orth += b;
+    t_rr += c;
+    double mx = -1.0;
+    int nin = 0;
+    for (int i = 0; i < m0; ++i)
+      if (h->theta[i] >= prm->lmin && h->theta[i] <= prm->lmax) {
+        ++nin;
+        mx = std::max(mx, res[i]);
+      }
+    if (nin > 0 && mx <= prm->outer_tol) {
+      status = RAFEAST_OK;
+      break;
+    }
+  }
+  if (it > prm->max_outer) it = prm->max_outer;
+  // outputs: in-interval pairs first (ascending), then the rest (ascending)
+  std::vector<int> order;
+  for (int i = 0; i < m0; ++i)
+    if (h->theta[i] >= prm->lmin && h->theta[i] <= prm->lmax) order.push_back(i);
+  const int mf = (int)order.size();
+  for (int i = 0; i < m0; ++i)
+    if (!(h->theta[i] >= prm->lmin && h->theta[i] <= prm->lmax)) order.push_back(i);
+  if (mf == 0) status = RAFEAST_NO_EIGENVALUE;
+  else if (mf >= m0) status = RAFEAST_M0_TOO_SMALL;
+  *m_found = mf;
+  std::vector<double> ev_out(m0), res_out(m0);
+  double maxres = 0.0;
+  for (int t = 0; t < m0; ++t) {
+    ev_out[t] = h->theta[order[t]];
+    res_out[t] = res[order[t]];
+    if (t < mf) maxres = std::max(maxres, res_out[t]);
+  }
+  if (outputs_on_device) {
+    RF_CUDA(cudaMemcpyAsync(evals, ev_out.data(), sizeof(double) * m0, cudaMemcpyHostToDevice,
+                            h->stream));
+    if (resid)
+      RF_CUDA(cudaMemcpyAsync(resid, res_out.data(), sizeof(double) * m0, cudaMemcpyHostToDevice,
+                              h->stream));
+  } else {
+    std::copy(ev_out.begin(), ev_out.end(), evals);
+    if (resid) std::copy(res_out.begin(), res_out.end(), resid);
+  }
+  if (evecs) {
+    int32_t* cols_d = (int32_t*)scratch(h, S_SMALL, sizeof(int32_t) * m0 + 64);
+    std::vector<int32_t> cols(order.begin(), order.end());
+    RF_CUDA(cudaMemcpyAsync(cols_d, cols.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice,
+                            h->stream));
+    export_block(h, h->Q, ldq, m0, cols_d, outputs_on_device, evecs);
+  }
+  RF_CUDA(cudaEventRecord(ev[5], h->stream));
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  float tot = 0, tws = 0;
+  cudaEventElapsedTime(&tot, ev[0], ev[5]);
+  cudaEventElapsedTime(&tws, ev[0], ev[1]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = status;
+    info->outer_iters = it;
+    info->cocg_iters_total = cocg_total;
+    info->cocg_min_last = fs.iters_min;
+    info->cocg_max_last = fs.iters_max;
+    info->cholqr_shifted = shifted_total;
+    info->kernel_launches = h->launches;
+    info->spmm_launches = h->spmm_launches;
+    info->max_resid = maxres;
+    info->t_warmstart_ms = tws;
+    info->t_filter_ms = t_filter;
+    info->t_orth_ms = t_orth;
+    info->t_rr_ms = t_rr;
+    info->t_total_ms = tot;
+  }
+  scope.finish();
+  return status;
+  API_END
+}
+
+int rafeast_solve_batched(int count, rafeast_t const* hs, const rafeast_params* prms,
+                          int* m_found, double* const* evals, double* const* evecs,
+                          double* const* resid, int outputs_on_device, rafeast_info* infos,
+                          int* statuses) {
+  if (count < 0 || (count > 0 && (!hs || !prms || !m_found || !evals || !statuses)))
+    return RAFEAST_ERR_INVALID_ARG;
+  int first_err = RAFEAST_OK;
+  for (int t = 0; t < count; ++t) {
+    const int rc = rafeast_solve(hs[t], &prms[t], &m_found[t], evals[t], evecs ? evecs[t] : nullptr,
+                                 resid ? resid[t] : nullptr, outputs_on_device,
+                                 infos ? &infos[t] : nullptr);
+    statuses[t] = rc;
+    if (rc < 0 && first_err == RAFEAST_OK) first_err = rc;
+  }
+  return first_err;
+}
+
+}  // extern "C"

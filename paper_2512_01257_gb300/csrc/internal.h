@@ -1,0 +1,215 @@
+// Internal interfaces of librafeast: handle layout, workspace, kernel
+// launchers. Not part of the public ABI (include/rafeast.h is).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <type_traits>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/rafeast.h"
+
+namespace rafeast {
+
+// ---- error plumbing ---------------------------------------------------------
+struct Err {
+  int code;
+};
+#define RF_CUDA(call)                                                      \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) {                                               \
+      ::rafeast::set_last_error(e_, #call, __FILE__, __LINE__);            \
+      throw ::rafeast::Err{e_ == cudaErrorMemoryAllocation                 \
+                               ? RAFEAST_ERR_OUT_OF_MEMORY                 \
+                               : RAFEAST_ERR_CUDA};                        \
+    }                                                                      \
+  } while (0)
+#define RF_LAUNCH() RF_CUDA(cudaGetLastError())
+#define RF_CHECK(cond, code)             \
+  do {                                   \
+    if (!(cond)) throw ::rafeast::Err{code}; \
+  } while (0)
+
+void set_last_error(cudaError_t e, const char* what, const char* file, int line);
+
+// ---- device control block of one batched COCG solve -------------------------
+struct CocgCtl {
+  unsigned int ticket;  // last-CTA election in the dot kernel
+  int iter;             // COCG iteration k about to run
+  int active;           // systems still iterating
+  int done;             // 1: every kernel of the solve returns at once
+  int breakdown;        // systems stopped by a vanishing p^T M p
+  int capped;           // systems stopped by max_inner
+  int max_iters;        // most iterations taken by any system
+  int min_iters;        // fewest iterations taken by a system with b != 0
+};
+
+// per-system scalar state, double precision (one struct per system s)
+struct SysState {
+  double2 gamma_prev;   // r_{k-1}^T r_{k-1}
+  double2 alpha_prev;   // alpha_{k-1}
+  double bnorm2;        // ||b||_2^2
+  int active;
+  int iters;
+};
+
+// per-system coefficients consumed by the update kernel, in working precision
+template <typename T> struct Coef {
+  typename std::conditional<sizeof(T) == 4, float2, double2>::type beta, alpha, ca;
+  T ar;
+  T pad;
+};
+
+// arguments of the batched COCG kernels (one problem or a concatenation)
+template <typename T> struct CocgArgs {
+  int64_t n;
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  const T* val;
+  int m0;          // subspace columns i
+  int ldc;         // complex stride of one state row (>= m0 * NC, even)
+  int lanes;       // G: lanes per row group (4, 8, 16, 32)
+  int cpl;         // chunks per lane (<= kernel's MAXCPL)
+  T* r[2];         // residual, ping-pong
+  T* p[2];         // search direction, ping-pong
+  T* dacc;         // quadrature accumulator, n x ldd (real)
+  int ldd;
+  const double* qin;     // Q, internal row-major n x ldq (init)
+  const double* aqin;    // A Q, same layout (correction form), or null
+  int ldq;
+  const double* theta;   // Ritz values [m0] (correction form)
+  const void* zs;        // c2<T>[NC]: z_j - sigma
+  const double2* coef;   // [nsys]: quadrature coefficient of system s
+  double* acc;           // [nsys * 5] dot partial sums (zeroed)
+  SysState* st;          // [nsys]
+  Coef<T>* cf;           // [nsys]
+  int* colact;           // [m0]: 1 while any shift of column i is active
+  CocgCtl* ctl;
+  int nc_real;           // shifts with a right-hand side (<= NC)
+  double tol2;           // solve_tol^2
+  int max_inner;
+  int form;              // RAFEAST_FORM_*
+};
+
+// ---- handle -----------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Handle {
+  int device = 0;
+  int num_sms = 0;
+  int64_t n = 0, nnz = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;  // internal, non-blocking
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // CSR in internal order
+  int32_t* rowptr = nullptr;
+  int32_t* colidx = nullptr;
+  double* val64 = nullptr;
+  float* val32 = nullptr;
+  double shift = 0.0;
+  double norm1 = 0.0, glo = 0.0, ghi = 0.0;
+  bool reordered = false;
+  int32_t* perm = nullptr;   // internal row r holds original row perm[r]
+  int32_t* iperm = nullptr;  // original row o sits at internal row iperm[o]
+  // current subspace (internal order, row-major n x ldq)
+  int m0 = 0, ldq = 0;
+  double* Q = nullptr;
+  double* AQ = nullptr;
+  std::vector<double> theta;  // host copy of Ritz values
+  double* theta_d = nullptr;
+  // options
+  int opt_ws_map = 0;
+  int opt_chunk = 16;
+  int opt_autotune = 1;
+  int opt_lanes = 0;
+  // scratch, grown on demand and kept
+  std::vector<DevBuf> bufs;
+  // launch accounting of the current call
+  int launches = 0;
+  int spmm_launches = 0;
+};
+
+void* scratch(Handle* h, int slot, size_t bytes);  // keep-alive buffer per slot
+enum Slot {
+  S_STATE = 0, S_DACC, S_QT, S_TMP1, S_TMP2, S_SCAL, S_GRAM, S_SMALL, S_OMEGA,
+  S_AQ2, S_IO1, S_IO2, S_COUNT
+};
+
+// ---- host math (hostmath.cpp) ------------------------------------------------
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+void quadrature_nodes(double lmin, double lmax, int nc, double e,
+                      std::vector<double>& zr, std::vector<double>& zi,
+                      std::vector<double>& wr, std::vector<double>& wi);
+// reverse Cuthill-McKee order of a symmetric CSR pattern: perm[new] = old
+void rcm_order(int64_t n, const int32_t* rowptr, const int32_t* colidx,
+               std::vector<int32_t>& perm);
+int64_t bandwidth(int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                  const int32_t* perm /* may be null */);
+
+// ---- kernel launchers (kernels_sparse.cu) --------------------------------------
+int nc_pad(int nc);  // shifts rounded up to a compiled NC (1, 2, 4, 8)
+int max_cpl(int NC, bool fp64);
+void choose_shape(int m0, int NC, bool fp64, int forced_lanes, int& lanes, int& cpl,
+                  int& colblocks);
+
+template <typename T>
+void launch_cocg_init(const CocgArgs<T>& a, int NC, int num_sms, cudaStream_t s);
+template <typename T>
+void launch_cocg_dots(const CocgArgs<T>& a, int NC, int buf, int num_sms, cudaStream_t s);
+template <typename T>
+void launch_cocg_update(const CocgArgs<T>& a, int NC, int buf, int num_sms, cudaStream_t s);
+
+// W = zs_j P - L P over complex chunks (rafeast_shifted_spmm)
+template <typename T>
+void launch_shifted_spmm(int64_t n, const int32_t* rp, const int32_t* ci, const T* val,
+                         int m, int ldc, int NC, const void* zs, const T* P, T* W,
+                         int lanes, int cpl, int num_sms, cudaStream_t s);
+// Y = sL * (L X) + sI * X, real, row-major n x ld (ld even)
+template <typename T>
+void launch_spmm_real(int64_t n, const int32_t* rp, const int32_t* ci, const T* val,
+                      int k, int ld, double sL, double sI, const T* X, T* Y,
+                      int num_sms, cudaStream_t s);
+
+// ---- dense kernels (kernels_dense.cu) ------------------------------------------
+void launch_philox(uint64_t seed, uint64_t first, int64_t nblocks, uint64_t* out,
+                   cudaStream_t s);
+void launch_omega(uint64_t seed, int64_t n, int k, double* out_colmajor, cudaStream_t s);
+// caller col-major (n x m, ld n, original order) <-> internal row-major (ld)
+void launch_to_internal(int64_t n, int m, const double* src, double* dst, int ld,
+                        const int32_t* perm, cudaStream_t s);
+void launch_from_internal(int64_t n, int m, const double* src, int ld, double* dst,
+                          const int32_t* perm, const int32_t* cols /* may be null */,
+                          cudaStream_t s);
+// row-major tall blocks, FP64
+void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
+          double* partial, int num_sms, cudaStream_t s);  // G = X^T Y (m x m, ld m)
+void tall_gemm(const double* X, int64_t n, int m, int ldx, const double* M, int mo,
+               double* Y, int ldy, cudaStream_t s);       // Y = X * M (M: m x mo, ld mo)
+// one-CTA Cholesky of G (+shift when needed) and inverse of the factor:
+// Rinv (m x m, ld m, upper) with Q R = X -> Q = X Rinv. status[0] = 0 ok,
+// 1 shifted, 2 failed; status[1..] unused.
+void chol_inv(double* G, int m, int64_t nrows, double* Rfac, double* Rinv, int* status,
+              cudaStream_t s);
+// one-CTA cyclic Jacobi: A (m x m, ld m, symmetric) -> eigenvalues ascending
+// in w, eigenvectors (columns) in V (m x m, ld m)
+void jacobi_eigh(double* A, int m, double* w, double* V, double* work, cudaStream_t s);
+// res_i = ||AQ_i - theta_i Q_i||^2 (sums, m), FP64
+void col_resid2(const double* Q, const double* AQ, const double* theta, int64_t n, int m,
+                int ld, double* out, cudaStream_t s);
+// Qt = f_i * Q + D (D in T, ld ldd)
+template <typename T>
+void launch_combine(const double* Q, int ldq, const T* D, int ldd, const double* f,
+                    int64_t n, int m, double* Qt, cudaStream_t s);
+void launch_zero(void* p, size_t bytes, cudaStream_t s);
+void launch_widen(const float* src, double* dst, int64_t count, cudaStream_t s);
+// out[i] = sum_r X[r][i] Y[r][i]
+void col_dot(const double* X, const double* Y, int64_t n, int m, int ld, double* out,
+             cudaStream_t s);
+void launch_cast_to_f32(const double* src, float* dst, int64_t count, cudaStream_t s);
+
+}  // namespace rafeast

@@ -1,0 +1,632 @@
+// Dense FP64 kernels of the RA-FEAST outer loop (sm_103a).
+//
+// * Philox-4x64-10 words and Box-Muller normals for Omega (Algorithm 2,
+//   "Draw Omega"; Salmon et al., SC'11).
+// * Layout moves between the caller's column-major blocks and the internal
+//   row-major, row-permuted blocks.
+// * Tall-skinny Gram G = X^T Y (Cholesky-QR Gram B_Q = Q~^T Q~ and the
+//   Rayleigh-Ritz matrix A_Q = Q^T (A Q), Algorithm 1), split over rows with
+//   per-CTA partials and a deterministic second-stage sum.
+// * One-CTA Cholesky of the m x m Gram matrix with the shift of shifted
+//   Cholesky-QR when it is not numerically positive definite (Fukaya,
+//   Kannan, Nakatsukasa, Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 2020),
+//   plus the inverse of the triangular factor, so Q = Q~ R^{-1} is a GEMM.
+// * Tall GEMM Y = X M (Q R^{-1}, Q V, (A Q) V).
+// * One-CTA cyclic Jacobi eigensolver for the reduced symmetric problem
+//   (Rayleigh-Ritz, Algorithm 1): round-robin ordering of m/2 disjoint
+//   rotations per round, rotation angles from the symmetric 2x2 Schur form.
+// * Column norms of A Q - Q diag(theta) (residuals) and column dots.
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace rafeast {
+
+// ---------------------------------------------------------------------------
+// Philox-4x64-10
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    const uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+__global__ void k_philox(uint64_t seed, uint64_t first, int64_t nblocks, uint64_t* out) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblocks;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t c[4] = {first + (uint64_t)b, 0, 0, 0};
+    philox4x64_10(c, seed, 0);
+    out[4 * b + 0] = c[0];
+    out[4 * b + 1] = c[1];
+    out[4 * b + 2] = c[2];
+    out[4 * b + 3] = c[3];
+  }
+}
+
+__device__ __forceinline__ double u01(uint64_t x) {
+  return ((double)(x >> 11) + 1.0) * 0x1.0p-53;
+}
+
+// Omega column-major n x k; linear index e = c*n + i; block e/4
+__global__ void k_omega(uint64_t seed, int64_t total, double* out) {
+  const int64_t nblk = (total + 3) / 4;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t c[4] = {(uint64_t)b, 0, 0, 0};
+    philox4x64_10(c, seed, 0);
+    double g[4];
+    {
+      const double rad = sqrt(-2.0 * log(u01(c[0])));
+      double s, co;
+      sincospi(2.0 * u01(c[1]), &s, &co);
+      g[0] = rad * co;
+      g[1] = rad * s;
+    }
+    {
+      const double rad = sqrt(-2.0 * log(u01(c[2])));
+      double s, co;
+      sincospi(2.0 * u01(c[3]), &s, &co);
+      g[2] = rad * co;
+      g[3] = rad * s;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (4 * b + t < total) out[4 * b + t] = g[t];
+  }
+}
+
+void launch_philox(uint64_t seed, uint64_t first, int64_t nblocks, uint64_t* out,
+                   cudaStream_t s) {
+  if (nblocks <= 0) return;
+  int64_t blocks = (nblocks + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_philox<<<(int)blocks, 256, 0, s>>>(seed, first, nblocks, out);
+  RF_LAUNCH();
+}
+
+void launch_omega(uint64_t seed, int64_t n, int k, double* out, cudaStream_t s) {
+  const int64_t total = n * (int64_t)k;
+  int64_t blocks = ((total + 3) / 4 + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  if (blocks < 1) blocks = 1;
+  k_omega<<<(int)blocks, 256, 0, s>>>(seed, total, out);
+  RF_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// layout moves
+// ---------------------------------------------------------------------------
+__global__ void k_to_internal(int64_t n, int m, const double* __restrict__ src,
+                              double* __restrict__ dst, int ld, const int32_t* __restrict__ perm) {
+  const int64_t total = n * (int64_t)ld;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ld;
+    const int c = (int)(e - r * ld);
+    const int64_t o = perm ? perm[r] : r;
+    dst[e] = c < m ? src[(int64_t)c * n + o] : 0.0;
+  }
+}
+
+__global__ void k_from_internal(int64_t n, int m, const double* __restrict__ src, int ld,
+                                double* __restrict__ dst, const int32_t* __restrict__ perm,
+                                const int32_t* __restrict__ cols) {
+  const int64_t total = n * (int64_t)m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / m;
+    const int c = (int)(e - r * m);
+    const int64_t o = perm ? perm[r] : r;
+    const int sc = cols ? cols[c] : c;
+    dst[(int64_t)c * n + o] = src[r * ld + sc];
+  }
+}
+
+static int blocks_for(int64_t total, int per = 256, int cap = 16384) {
+  int64_t b = (total + per - 1) / per;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+void launch_to_internal(int64_t n, int m, const double* src, double* dst, int ld,
+                        const int32_t* perm, cudaStream_t s) {
+  k_to_internal<<<blocks_for(n * (int64_t)ld), 256, 0, s>>>(n, m, src, dst, ld, perm);
+  RF_LAUNCH();
+}
+
+void launch_from_internal(int64_t n, int m, const double* src, int ld, double* dst,
+                          const int32_t* perm, const int32_t* cols, cudaStream_t s) {
+  if (m <= 0) return;
+  k_from_internal<<<blocks_for(n * (int64_t)m), 256, 0, s>>>(n, m, src, ld, dst, perm, cols);
+  RF_LAUNCH();
+}
+
+__global__ void k_cast_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (float)src[e];
+}
+void launch_cast_to_f32(const double* src, float* dst, int64_t count, cudaStream_t s) {
+  if (count <= 0) return;
+  k_cast_f32<<<blocks_for(count), 256, 0, s>>>(src, dst, count);
+  RF_LAUNCH();
+}
+
+__global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (double)src[e];
+}
+void launch_widen(const float* src, double* dst, int64_t count, cudaStream_t s) {
+  if (count <= 0) return;
+  k_widen<<<blocks_for(count), 256, 0, s>>>(src, dst, count);
+  RF_LAUNCH();
+}
+
+void launch_zero(void* p, size_t bytes, cudaStream_t s) {
+  if (bytes) RF_CUDA(cudaMemsetAsync(p, 0, bytes, s));
+}
+
+// ---------------------------------------------------------------------------
+// tall-skinny Gram: partial[cta] = X[rows]^T Y[rows], then a column sum
+// ---------------------------------------------------------------------------
+constexpr int GRAM_RB = 16;
+
+template <int U>
+__global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ X,
+                                                      const double* __restrict__ Y, int64_t n,
+                                                      int m, int ld, double* __restrict__ part) {
+  extern __shared__ double gsm[];
+  double* Xs = gsm;                 // [GRAM_RB][ld]
+  double* Ys = gsm + GRAM_RB * ld;  // [GRAM_RB][ld]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[U][U];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = blockIdx.x * chunk;
+  const int64_t r1 = min(n, r0 + chunk);
+  for (int64_t rb = r0; rb < r1; rb += GRAM_RB) {
+    const int rows = (int)min((int64_t)GRAM_RB, r1 - rb);
+    __syncthreads();
+    for (int t = threadIdx.x; t < GRAM_RB * ld; t += blockDim.x) {
+      const int rr = t / ld;
+      Xs[t] = rr < rows ? X[(rb + rr) * ld + (t - rr * ld)] : 0.0;
+      Ys[t] = rr < rows ? Y[(rb + rr) * ld + (t - rr * ld)] : 0.0;
+    }
+    __syncthreads();
+    for (int rr = 0; rr < rows; ++rr) {
+      double xa[U], yb[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int a = tx + 16 * u;
+        xa[u] = a < m ? Xs[rr * ld + a] : 0.0;
+        const int b = ty + 16 * u;
+        yb[u] = b < m ? Ys[rr * ld + b] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < U; ++v) acc[u][v] = fma(xa[u], yb[v], acc[u][v]);
+    }
+  }
+  double* out = part + (int64_t)blockIdx.x * m * m;
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      const int a = tx + 16 * u, b = ty + 16 * v;
+      if (a < m && b < m) out[a * m + b] = acc[u][v];
+    }
+}
+
+__global__ void k_gram_sum(const double* __restrict__ part, int nparts, int mm, double* G) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * mm + e];
+    G[e] = s;
+  }
+}
+
+int gram_parts(int num_sms) { return 2 * num_sms; }
+
+void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
+          double* partial, int num_sms, cudaStream_t s) {
+  const int U = (m + 15) / 16;
+  const int parts = gram_parts(num_sms);
+  const size_t smem = 2 * GRAM_RB * (size_t)ld * sizeof(double);
+  switch (U) {
+#define RF_GRAM(UU)                                                                   \
+  case UU:                                                                            \
+    cudaFuncSetAttribute(k_gram_partial<UU>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                         (int)smem);                                                  \
+    k_gram_partial<UU><<<parts, 256, smem, s>>>(X, Y, n, m, ld, partial);             \
+    break;
+    RF_GRAM(1) RF_GRAM(2) RF_GRAM(3) RF_GRAM(4) RF_GRAM(5) RF_GRAM(6) RF_GRAM(7) RF_GRAM(8)
+#undef RF_GRAM
+    default: throw Err{RAFEAST_ERR_INVALID_ARG};
+  }
+  RF_LAUNCH();
+  k_gram_sum<<<(m * m + 255) / 256, 256, 0, s>>>(partial, parts, m * m, G);
+  RF_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// tall GEMM: Y[r][b] = sum_a X[r][a] M[a][b]   (M row-major m x mo)
+// ---------------------------------------------------------------------------
+constexpr int GEMM_ROWS = 8;
+
+template <int V>
+__global__ void __launch_bounds__(256) k_tall_gemm(const double* __restrict__ X, int64_t n, int m,
+                                                   int ldx, const double* __restrict__ M, int mo,
+                                                   double* __restrict__ Y, int ldy) {
+  extern __shared__ double tsm[];
+  double* Ms = tsm;              // m * mo
+  double* Xs = tsm + m * mo;     // GEMM_ROWS * m
+  for (int t = threadIdx.x; t < m * mo; t += blockDim.x) Ms[t] = M[t];
+  const int tr = threadIdx.x >> 5, tc = threadIdx.x & 31;
+  for (int64_t rb = blockIdx.x * (int64_t)GEMM_ROWS; rb < n; rb += (int64_t)gridDim.x * GEMM_ROWS) {
+    __syncthreads();
+    const int rows = (int)min((int64_t)GEMM_ROWS, n - rb);
+    for (int t = threadIdx.x; t < GEMM_ROWS * m; t += blockDim.x) {
+      const int rr = t / m;
+      Xs[t] = rr < rows ? X[(rb + rr) * ldx + (t - rr * m)] : 0.0;
+    }
+    __syncthreads();
+    if (tr < rows) {
+      double acc[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = 0.0;
+      for (int a = 0; a < m; ++a) {
+        const double x = Xs[tr * m + a];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int b = tc + 32 * v;
+          if (b < mo) acc[v] = fma(x, Ms[a * mo + b], acc[v]);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int b = tc + 32 * v;
+        if (b < mo) Y[(rb + tr) * ldy + b] = acc[v];
+      }
+    }
+  }
+}
+
+void tall_gemm(const double* X, int64_t n, int m, int ldx, const double* M, int mo, double* Y,
+               int ldy, cudaStream_t s) {
+  const int V = (mo + 31) / 32;
+  const size_t smem = ((size_t)m * mo + (size_t)GEMM_ROWS * m) * sizeof(double);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (n + GEMM_ROWS - 1) / GEMM_ROWS;
+  int blocks = (int)std::min<int64_t>(tiles, (int64_t)sms * 2);
+  if (blocks < 1) blocks = 1;
+  switch (V) {
+#define RF_TG(VV)                                                                     \
+  case VV:                                                                            \
+    cudaFuncSetAttribute(k_tall_gemm<VV>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                         (int)smem);                                                  \
+    k_tall_gemm<VV><<<blocks, 256, smem, s>>>(X, n, m, ldx, M, mo, Y, ldy);           \
+    break;
+    RF_TG(1) RF_TG(2) RF_TG(3) RF_TG(4)
+#undef RF_TG
+    default: throw Err{RAFEAST_ERR_INVALID_ARG};
+  }
+  RF_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// one-CTA Cholesky (+shift) and triangular inverse
+// G: m x m (row-major, symmetric). Outputs R (upper, G = R^T R, row-major) and
+// Rinv (upper, row-major); status: 0 ok, 1 shifted, 2 failed.
+// ---------------------------------------------------------------------------
+__device__ bool chol_inplace(double* S, int m) {
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = S[k * m + k];
+      if (!(d > 0.0) || !isfinite(d)) s_bad = 1;
+      else S[k * m + k] = sqrt(d);
+    }
+    __syncthreads();
+    if (s_bad) return false;
+    const double dk = S[k * m + k];
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) S[i * m + k] /= dk;
+    __syncthreads();
+    const int rem = m - k - 1;
+    const int tot = rem * rem;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int i = k + 1 + t / rem, j = k + 1 + t % rem;
+      if (j <= i) S[i * m + j] -= S[i * m + k] * S[j * m + k];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+__global__ void k_chol_inv(const double* __restrict__ G, int m, double shift_scale,
+                           double* __restrict__ R, double* __restrict__ Rinv, int* status) {
+  extern __shared__ double S[];  // m*m
+  __shared__ double s_shift;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) S[t] = G[t];
+  __syncthreads();
+  int st = 0;
+  bool ok = chol_inplace(S, m);
+  if (!ok) {
+    // shifted Cholesky-QR: s = 11 (n m + m (m + 1)) u ||X||_2^2, ||X||_2^2 <= trace(G)
+    if (threadIdx.x == 0) {
+      double tr = 0.0;
+      for (int i = 0; i < m; ++i) tr += fabs(G[i * m + i]);
+      s_shift = shift_scale * tr;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int i = t / m, j = t % m;
+      S[t] = G[t] + (i == j ? s_shift : 0.0);
+    }
+    __syncthreads();
+    ok = chol_inplace(S, m);
+    st = ok ? 1 : 2;
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) status[0] = 2;
+    return;
+  }
+  // R = L^T (upper)
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int i = t / m, j = t % m;
+    R[t] = j >= i ? S[j * m + i] : 0.0;
+  }
+  // Linv by forward substitution, one column per thread; Rinv = Linv^T
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    for (int i = 0; i < m; ++i) {
+      double x;
+      if (i < j) {
+        x = 0.0;
+      } else {
+        double acc = (i == j) ? 1.0 : 0.0;
+        for (int k = j; k < i; ++k) acc -= S[i * m + k] * Rinv[j * m + k];
+        x = acc / S[i * m + i];
+      }
+      Rinv[j * m + i] = x;  // row j of Rinv holds column j of Linv^T... see below
+    }
+  }
+  __syncthreads();
+  // Rinv currently holds Linv^T stored as Rinv[j][i] = Linv[i][j] = (Linv^T)[j][i]
+  if (threadIdx.x == 0) status[0] = st;
+}
+
+void chol_inv(double* G, int m, int64_t nrows, double* Rfac, double* Rinv, int* status,
+              cudaStream_t s) {
+  const size_t smem = (size_t)m * m * sizeof(double);
+  cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const double u = DBL_EPSILON / 2;
+  const double scale = 11.0 * ((double)nrows * m + (double)m * (m + 1)) * u;
+  k_chol_inv<<<1, 256, smem, s>>>(G, m, scale, Rfac, Rinv, status);
+  RF_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// one-CTA cyclic Jacobi (round-robin parallel order)
+// ---------------------------------------------------------------------------
+__global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restrict__ w,
+                         double* __restrict__ Vout, double* __restrict__ Vw, int max_sweeps) {
+  extern __shared__ double A[];  // me * me, me = m rounded up to even
+  const int me = m + (m & 1);
+  __shared__ double cs[64 * 2];  // c, s per pair (me/2 <= 64)
+  __shared__ int pq[64 * 2];
+  __shared__ double s_off, s_tot;
+  __shared__ int s_order[128];
+  for (int t = threadIdx.x; t < me * me; t += blockDim.x) {
+    const int i = t / me, j = t % me;
+    A[t] = (i < m && j < m) ? 0.5 * (Ain[i * m + j] + Ain[j * m + i]) : 0.0;
+    Vw[t] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int np = me / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence test on the off-diagonal mass
+    if (threadIdx.x == 0) {
+      s_off = 0.0;
+      s_tot = 0.0;
+    }
+    __syncthreads();
+    double off = 0.0, tot = 0.0;
+    for (int t = threadIdx.x; t < me * me; t += blockDim.x) {
+      const int i = t / me, j = t % me;
+      const double a2 = A[t] * A[t];
+      tot += a2;
+      if (i != j) off += a2;
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&s_off, off);
+      atomicAdd(&s_tot, tot);
+    }
+    __syncthreads();
+    if (!(s_off > 1e-32 * s_tot) || s_tot == 0.0) break;
+    for (int round = 0; round < me - 1; ++round) {
+      for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        // circle method: position 0 fixed, others rotate
+        auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (me - 1)) + 1; };
+        int p = player(k), q = player(me - 1 - k);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        const double apq = A[p * me + q];
+        double c = 1.0, s = 0.0;
+        const double app = A[p * me + p], aqq = A[q * me + q];
+        if (apq != 0.0 && fabs(apq) > 1e-300 &&
+            fabs(apq) > 1e-17 * sqrt(fabs(app * aqq))) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double at = fabs(tau);
+          const double root = at > 1e150 ? at : sqrt(1.0 + tau * tau);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (at + root);
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        cs[2 * k] = c;
+        cs[2 * k + 1] = s;
+        pq[2 * k] = p;
+        pq[2 * k + 1] = q;
+      }
+      __syncthreads();
+      // rows: (J^T A)
+      for (int t = threadIdx.x; t < np * me; t += blockDim.x) {
+        const int k = t / me, col = t % me;
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        if (s == 0.0) continue;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        const double ap = A[p * me + col], aq = A[q * me + col];
+        A[p * me + col] = c * ap - s * aq;
+        A[q * me + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: (A J) and V J
+      for (int t = threadIdx.x; t < np * me; t += blockDim.x) {
+        const int k = t / me, row = t % me;
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        if (s == 0.0) continue;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        const double ap = A[row * me + p], aq = A[row * me + q];
+        A[row * me + p] = c * ap - s * aq;
+        A[row * me + q] = s * ap + c * aq;
+        const double vp = Vw[row * me + p], vq = Vw[row * me + q];
+        Vw[row * me + p] = c * vp - s * vq;
+        Vw[row * me + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        if (cs[2 * k + 1] == 0.0) continue;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        A[p * me + q] = 0.0;
+        A[q * me + p] = 0.0;
+      }
+      __syncthreads();
+    }
+  }
+  // sort eigenvalues ascending (m <= 128), then write w and V columns
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < m; ++i) s_order[i] = i;
+    for (int i = 1; i < m; ++i) {
+      const int key = s_order[i];
+      const double kv = A[key * me + key];
+      int j = i - 1;
+      while (j >= 0 && A[s_order[j] * me + s_order[j]] > kv) {
+        s_order[j + 1] = s_order[j];
+        --j;
+      }
+      s_order[j + 1] = key;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = A[s_order[i] * me + s_order[i]];
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int r = t / m, c = t % m;
+    Vout[r * m + c] = Vw[r * me + s_order[c]];
+  }
+}
+
+void jacobi_eigh(double* A, int m, double* w, double* V, double* work, cudaStream_t s) {
+  if (m > 128) throw Err{RAFEAST_ERR_INVALID_ARG};
+  const int me = m + (m & 1);
+  const size_t smem = (size_t)me * me * sizeof(double);
+  cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_jacobi<<<1, 512, smem, s>>>(A, m, w, V, work, 40);
+  RF_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// column reductions over rows
+// mode 0: out[i] = sum_r X[r][i] Y[r][i];  mode 1: out[i] = sum_r (Y - th_i X)^2
+// ---------------------------------------------------------------------------
+__global__ void k_colred(const double* __restrict__ X, const double* __restrict__ Y,
+                         const double* __restrict__ th, int64_t n, int m, int ld, int mode,
+                         double* out) {
+  const int i = threadIdx.x;
+  if (i >= m) return;
+  const double t = mode ? th[i] : 0.0;
+  double acc = 0.0;
+  for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+    const double x = X[r * ld + i], y = Y[r * ld + i];
+    if (mode) {
+      const double d = y - t * x;
+      acc = fma(d, d, acc);
+    } else {
+      acc = fma(x, y, acc);
+    }
+  }
+  atomicAdd(out + i, acc);
+}
+
+void col_dot(const double* X, const double* Y, int64_t n, int m, int ld, double* out,
+             cudaStream_t s) {
+  RF_CUDA(cudaMemsetAsync(out, 0, m * sizeof(double), s));
+  const int threads = ((m + 31) / 32) * 32;
+  int blocks = (int)std::min<int64_t>(n, 1024);
+  k_colred<<<blocks, threads, 0, s>>>(X, Y, nullptr, n, m, ld, 0, out);
+  RF_LAUNCH();
+}
+
+void col_resid2(const double* Q, const double* AQ, const double* theta, int64_t n, int m, int ld,
+                double* out, cudaStream_t s) {
+  RF_CUDA(cudaMemsetAsync(out, 0, m * sizeof(double), s));
+  const int threads = ((m + 31) / 32) * 32;
+  int blocks = (int)std::min<int64_t>(n, 1024);
+  k_colred<<<blocks, threads, 0, s>>>(Q, AQ, theta, n, m, ld, theta ? 1 : 0, out);
+  RF_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// quadrature combine: Qt = f_i Q + D
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_combine(const double* __restrict__ Q, int ldq, const T* __restrict__ D, int ldd,
+                          const double* __restrict__ f, int64_t n, int m, double* __restrict__ Qt) {
+  const int64_t total = n * (int64_t)m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / m;
+    const int i = (int)(e - r * m);
+    Qt[r * ldq + i] = fma(f[i], Q[r * ldq + i], (double)D[r * ldd + i]);
+  }
+}
+
+template <typename T>
+void launch_combine(const double* Q, int ldq, const T* D, int ldd, const double* f, int64_t n,
+                    int m, double* Qt, cudaStream_t s) {
+  k_combine<T><<<blocks_for(n * (int64_t)m), 256, 0, s>>>(Q, ldq, D, ldd, f, n, m, Qt);
+  RF_LAUNCH();
+}
+template void launch_combine<float>(const double*, int, const float*, int, const double*, int64_t,
+                                    int, double*, cudaStream_t);
+template void launch_combine<double>(const double*, int, const double*, int, const double*,
+                                     int64_t, int, double*, cudaStream_t);
+
+}  // namespace rafeast

@@ -1,0 +1,714 @@
+// Sparse kernels of the RA-FEAST hot path (sm_103a).
+//
+// 1. Batched COCG for the shifted systems (z_j I - A) X_j = B of Algorithm 1 /
+//    Algorithm 2 Step 2a, all N_c shifts x m0 columns in one launch. Each
+//    COCG step is two launches (Chronopoulos-Gear ordering of the CG scalars:
+//    one global reduction per step):
+//      dots   : w = M r_k with M = (z_j - sigma) I - L, gathered from r_k;
+//               gamma = r^T r, delta = r^T w, nu = ||r||^2 (Hermitian) per
+//               system; the last CTA turns them into alpha_k, beta_k in FP64.
+//      update : p_k = r_k + beta_k p_{k-1}, s = M p_k recomputed from the
+//               gathered r_k and p_{k-1} (no stored w/s vector),
+//               r_{k+1} = r_k - alpha_k s, and the quadrature sum
+//               D += Re(c_js alpha_k p_k) (x is never stored).
+//    Per step the state is streamed 5.5 times (n x ldc complex) instead of the
+//    11 times of the textbook three-kernel form with stored x and w.
+// 2. Plain SpMM variants with the same gather core: W = zs P - L P (complex,
+//    for rafeast_shifted_spmm) and Y = sL (L X) + sI X (real; warmstart powers
+//    and Rayleigh-Ritz products).
+//
+// Work mapping: a CTA has 8 warps; a warp is split into groups of G lanes
+// (G = 4..32); each group owns one row at a time (grid-stride over rows so
+// all CTAs sweep A's rows together and gathered rows are reused in L2);
+// lane l of a group owns column chunks i = base + l + c*G, c < cpl, each chunk
+// holding the NC shifts of subspace column i.
+#include <cstdio>
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace rafeast {
+
+constexpr int WARPS = 8;
+constexpr int THREADS = WARPS * 32;
+
+template <typename T> constexpr int maxcpl_of(int NC);
+template <> constexpr int maxcpl_of<float>(int NC) { return NC >= 12 ? 1 : 12 / NC; }
+template <> constexpr int maxcpl_of<double>(int NC) { return NC >= 8 ? 1 : 8 / NC; }
+
+int nc_pad(int nc) {
+  if (nc <= 1) return 1;
+  if (nc <= 2) return 2;
+  if (nc <= 4) return 4;
+  return 8;
+}
+int max_cpl(int NC, bool fp64) { return fp64 ? maxcpl_of<double>(NC) : maxcpl_of<float>(NC); }
+
+void choose_shape(int m0, int NC, bool fp64, int forced_lanes, int& lanes, int& cpl,
+                  int& colblocks) {
+  const int mc = max_cpl(NC, fp64);
+  double best = -1.0;
+  const int cands[4] = {32, 16, 8, 4};
+  for (int t = 0; t < 4; ++t) {
+    int G = cands[t];
+    if (forced_lanes && G != forced_lanes) continue;
+    int c = (m0 + G - 1) / G;
+    if (c > mc) c = mc;
+    int blocks = (m0 + G * c - 1) / (G * c);
+    double eff = double(m0) / double(blocks * G * c);
+    // prefer wide groups (fewer re-reads of A) unless much less efficient
+    double score = eff - 0.02 * (blocks - 1);
+    if (score > best + 1e-12) {
+      best = score;
+      lanes = G;
+      cpl = c;
+      colblocks = blocks;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// gather core: acc[c][j] += sum_k val_k * X[col_k][chunk c], chunk active mask
+// ---------------------------------------------------------------------------
+template <typename T, int NC, int MAXCPL>
+__device__ __forceinline__ void gather_row(const int32_t* __restrict__ colidx,
+                                           const T* __restrict__ val, int k0, int k1,
+                                           const T* __restrict__ X, int64_t ldx_t,
+                                           const int (&coff)[MAXCPL], unsigned mask,
+                                           c2<T> (&acc)[MAXCPL][NC]) {
+  using C = c2<T>;
+  int k = k0;
+  for (; k + 1 < k1; k += 2) {
+    const int ca = __ldg(colidx + k), cb = __ldg(colidx + k + 1);
+    const T va = __ldg(val + k), vb = __ldg(val + k + 1);
+    C xa[MAXCPL][NC], xb[MAXCPL][NC];
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+      if (mask & (1u << c)) {
+        ld_chunk<NC>(X + (int64_t)ca * ldx_t + coff[c], xa[c]);
+        ld_chunk<NC>(X + (int64_t)cb * ldx_t + coff[c], xb[c]);
+      }
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+      if (mask & (1u << c)) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          acc[c][j] = crfma<T>(va, xa[c][j], acc[c][j]);
+          acc[c][j] = crfma<T>(vb, xb[c][j], acc[c][j]);
+        }
+      }
+  }
+  if (k < k1) {
+    const int ca = __ldg(colidx + k);
+    const T va = __ldg(val + k);
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+      if (mask & (1u << c)) {
+        C xa[NC];
+        ld_chunk<NC>(X + (int64_t)ca * ldx_t + coff[c], xa);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[c][j] = crfma<T>(va, xa[j], acc[c][j]);
+      }
+  }
+}
+
+// two arrays at once (update kernel): acc_r from R, acc_p from P
+template <typename T, int NC, int MAXCPL>
+__device__ __forceinline__ void gather_row2(const int32_t* __restrict__ colidx,
+                                            const T* __restrict__ val, int k0, int k1,
+                                            const T* __restrict__ R, const T* __restrict__ P,
+                                            int64_t ldx_t, const int (&coff)[MAXCPL],
+                                            unsigned mask, c2<T> (&ar)[MAXCPL][NC],
+                                            c2<T> (&ap)[MAXCPL][NC]) {
+  using C = c2<T>;
+  for (int k = k0; k < k1; ++k) {
+    const int ca = __ldg(colidx + k);
+    const T va = __ldg(val + k);
+    C xr[MAXCPL][NC], xp[MAXCPL][NC];
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+      if (mask & (1u << c)) {
+        ld_chunk<NC>(R + (int64_t)ca * ldx_t + coff[c], xr[c]);
+        ld_chunk<NC>(P + (int64_t)ca * ldx_t + coff[c], xp[c]);
+      }
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+      if (mask & (1u << c)) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          ar[c][j] = crfma<T>(va, xr[c][j], ar[c][j]);
+          ap[c][j] = crfma<T>(va, xp[c][j], ap[c][j]);
+        }
+      }
+  }
+}
+
+struct RowMap {
+  int lg, G, cpl;
+  int64_t gid, gstride;
+};
+
+__device__ __forceinline__ RowMap row_map(int G, int cpl) {
+  RowMap m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gpw = 32 / G;
+  m.G = G;
+  m.cpl = cpl;
+  m.lg = lane % G;
+  m.gid = ((int64_t)blockIdx.x * WARPS + warp) * gpw + lane / G;
+  m.gstride = (int64_t)gridDim.x * WARPS * gpw;
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// COCG: reset of the small per-system arrays
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_cocg_reset(CocgArgs<T> a, int NC) {
+  const int nsys = a.m0 * NC;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+    SysState st;
+    st.gamma_prev = make_double2(1.0, 0.0);
+    st.alpha_prev = make_double2(1.0, 0.0);
+    st.bnorm2 = 0.0;
+    st.active = 1;
+    st.iters = 0;
+    a.st[s] = st;
+    for (int q = 0; q < 5; ++q) a.acc[5 * s + q] = 0.0;
+    if (s % NC == 0) a.colact[s / NC] = 1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    CocgCtl c;
+    c.ticket = 0;
+    c.iter = 0;
+    c.active = nsys;
+    c.done = 0;
+    c.breakdown = 0;
+    c.capped = 0;
+    c.max_iters = 0;
+    c.min_iters = 0;
+    *a.ctl = c;
+  }
+}
+
+// init: r0 = b (real rhs, zero imaginary part), p_{-1} = 0, D = 0
+template <typename T, int NC>
+__global__ void __launch_bounds__(THREADS) k_cocg_init(CocgArgs<T> a) {
+  using C = c2<T>;
+  const int64_t total = a.n * (int64_t)a.m0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = e / a.m0;
+    const int i = (int)(e - row * a.m0);
+    double b = a.qin[row * a.ldq + i];
+    if (a.form == RAFEAST_FORM_CORRECTION) b = a.aqin[row * a.ldq + i] - a.theta[i] * b;
+    C rv[NC], pv[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      rv[j] = mk<T>(j < a.nc_real ? (T)b : (T)0, (T)0);
+      pv[j] = mk<T>((T)0, (T)0);
+    }
+    const int64_t off = (row * a.ldc + (int64_t)i * NC) * 2;
+    st_chunk<NC>(a.r[0] + off, rv);
+    st_chunk<NC>(a.p[0] + off, pv);
+    a.dacc[row * a.ldd + i] = (T)0;
+  }
+}
+
+// scalar step of the last CTA: alpha_k, beta_k per system from the sums
+template <typename T>
+__device__ void cocg_scalar_step(const CocgArgs<T>& a, int NC) {
+  using C = c2<T>;
+  __shared__ int s_active, s_brk, s_cap, s_max, s_min;
+  if (threadIdx.x == 0) {
+    s_active = 0;
+    s_brk = 0;
+    s_cap = 0;
+    s_max = 0;
+    s_min = 0x7fffffff;
+  }
+  __syncthreads();
+  const int k = __ldcg(&a.ctl->iter);
+  const int nsys = a.m0 * NC;
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+    SysState st = a.st[s];
+    double* acc = a.acc + 5 * s;
+    const double gre = __ldcg(acc + 0), gim = __ldcg(acc + 1);
+    const double dre = __ldcg(acc + 2), dim = __ldcg(acc + 3), nu = __ldcg(acc + 4);
+    acc[0] = acc[1] = acc[2] = acc[3] = acc[4] = 0.0;
+    Coef<T> cf;
+    cf.pad = (T)0;
+    bool freeze = !st.active;
+    if (st.active) {
+      if (k == 0) st.bnorm2 = nu;
+      const bool conv = nu <= a.tol2 * st.bnorm2;
+      if (conv || k >= a.max_inner) {
+        st.active = 0;
+        st.iters = k;
+        freeze = true;
+        if (!conv) atomicAdd(&s_cap, 1);
+        if (st.bnorm2 > 0.0) {
+          atomicMax(&s_max, k);
+          atomicMin(&s_min, k);
+        }
+      } else {
+        double bre = 0.0, bim = 0.0, mre = dre, mim = dim;
+        if (k > 0) {
+          // beta = gamma / gamma_prev
+          const double2 gp = st.gamma_prev;
+          const double den = gp.x * gp.x + gp.y * gp.y;
+          bre = (gre * gp.x + gim * gp.y) / den;
+          bim = (gim * gp.x - gre * gp.y) / den;
+          // mu = delta - beta * gamma / alpha_prev
+          const double2 ap = st.alpha_prev;
+          const double da = ap.x * ap.x + ap.y * ap.y;
+          const double bgr = bre * gre - bim * gim, bgi = bre * gim + bim * gre;
+          mre = dre - (bgr * ap.x + bgi * ap.y) / da;
+          mim = dim - (bgi * ap.x - bgr * ap.y) / da;
+        }
+        const double mabs = fabs(mre) + fabs(mim);
+        if (!(mabs > 1e-300) || !isfinite(mabs) || !isfinite(bre) || !isfinite(bim)) {
+          st.active = 0;
+          st.iters = k;
+          freeze = true;
+          atomicAdd(&s_brk, 1);
+        } else {
+          const double mm = mre * mre + mim * mim;
+          const double are = (gre * mre + gim * mim) / mm;
+          const double aim = (gim * mre - gre * mim) / mm;
+          st.gamma_prev = make_double2(gre, gim);
+          st.alpha_prev = make_double2(are, aim);
+          const double2 cq = a.coef[s];
+          cf.ar = (T)1;
+          cf.beta = mk<T>((T)bre, (T)bim);
+          cf.alpha = mk<T>((T)are, (T)aim);
+          cf.ca = mk<T>((T)(cq.x * are - cq.y * aim), (T)(cq.x * aim + cq.y * are));
+          atomicAdd(&s_active, 1);
+        }
+      }
+    }
+    if (freeze) {
+      cf.ar = (T)0;
+      cf.beta = mk<T>((T)1, (T)0);
+      cf.alpha = mk<T>((T)0, (T)0);
+      cf.ca = mk<T>((T)0, (T)0);
+    }
+    a.st[s] = st;
+    a.cf[s] = cf;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.m0; i += blockDim.x) {
+    int any = 0;
+    for (int j = 0; j < NC; ++j) any |= a.st[i * NC + j].active;
+    a.colact[i] = any;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    CocgCtl* c = a.ctl;
+    c->active = s_active;
+    c->breakdown += s_brk;
+    c->capped += s_cap;
+    if (s_max > c->max_iters) c->max_iters = s_max;
+    if (s_min != 0x7fffffff && (c->min_iters == 0 || s_min < c->min_iters)) c->min_iters = s_min;
+    c->iter = k + 1;
+    if (s_active == 0) c->done = 1;
+    __threadfence();
+    c->ticket = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// COCG dots kernel
+// ---------------------------------------------------------------------------
+template <typename T, int NC, int MAXCPL>
+__global__ void __launch_bounds__(THREADS) k_cocg_dots(CocgArgs<T> a, int buf) {
+  using C = c2<T>;
+  if (__ldcg(&a.ctl->done)) return;
+  const RowMap mp = row_map(a.lanes, a.cpl);
+  const int ibase = blockIdx.y * mp.G * mp.cpl + mp.lg;
+  const T* __restrict__ R = a.r[buf];
+  const int64_t ldt = (int64_t)a.ldc * 2;
+  const C* zs = reinterpret_cast<const C*>(a.zs);
+  C zv[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) zv[j] = zs[j];
+  int coff[MAXCPL];
+  unsigned mask = 0;
+#pragma unroll
+  for (int c = 0; c < MAXCPL; ++c) {
+    const int i = ibase + c * mp.G;
+    coff[c] = i * NC * 2;
+    if (c < mp.cpl && i < a.m0 && __ldcg(a.colact + i)) mask |= 1u << c;
+  }
+  // per-lane partial dots in working precision
+  T dg_re[MAXCPL][NC], dg_im[MAXCPL][NC], dd_re[MAXCPL][NC], dd_im[MAXCPL][NC], dn[MAXCPL][NC];
+#pragma unroll
+  for (int c = 0; c < MAXCPL; ++c)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) dg_re[c][j] = dg_im[c][j] = dd_re[c][j] = dd_im[c][j] = dn[c][j] = (T)0;
+
+  if (mask) {
+    for (int64_t row = mp.gid; row < a.n; row += mp.gstride) {
+      const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
+      C acc[MAXCPL][NC];
+#pragma unroll
+      for (int c = 0; c < MAXCPL; ++c)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[c][j] = mk<T>((T)0, (T)0);
+      gather_row<T, NC, MAXCPL>(a.colidx, a.val, k0, k1, R, ldt, coff, mask, acc);
+#pragma unroll
+      for (int c = 0; c < MAXCPL; ++c)
+        if (mask & (1u << c)) {
+          C rv[NC];
+          ld_chunk<NC>(R + row * ldt + coff[c], rv);
+#pragma unroll
+          for (int j = 0; j < NC; ++j) {
+            const C w = csub<T>(cmul<T>(zv[j], rv[j]), acc[c][j]);
+            // gamma += r r, delta += r w, nu += |r|^2
+            dg_re[c][j] = fma(rv[j].x, rv[j].x, fma(-rv[j].y, rv[j].y, dg_re[c][j]));
+            dg_im[c][j] = fma((T)2 * rv[j].x, rv[j].y, dg_im[c][j]);
+            dd_re[c][j] = fma(rv[j].x, w.x, fma(-rv[j].y, w.y, dd_re[c][j]));
+            dd_im[c][j] = fma(rv[j].x, w.y, fma(rv[j].y, w.x, dd_im[c][j]));
+            dn[c][j] = fma(rv[j].x, rv[j].x, fma(rv[j].y, rv[j].y, dn[c][j]));
+          }
+        }
+    }
+  }
+  // reduce: groups of a warp -> smem (double) -> global atomics
+  extern __shared__ double sred[];  // [G * MAXCPL * NC * 5]
+  const int nred = mp.G * MAXCPL * NC * 5;
+  for (int t = threadIdx.x; t < nred; t += blockDim.x) sred[t] = 0.0;
+  __syncthreads();
+  // every lane of the warp takes part in every shuffle (lanes without work
+  // hold zeros), so the full-mask shuffles are never divergent
+#pragma unroll
+  for (int c = 0; c < MAXCPL; ++c)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      double v[5] = {(double)dg_re[c][j], (double)dg_im[c][j], (double)dd_re[c][j],
+                     (double)dd_im[c][j], (double)dn[c][j]};
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        double x = v[q];
+        for (int o = mp.G; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        v[q] = x;
+      }
+      if ((threadIdx.x & 31) < mp.G && (mask & (1u << c))) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) atomicAdd(&sred[((mp.lg * MAXCPL + c) * NC + j) * 5 + q], v[q]);
+      }
+    }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nred; t += blockDim.x) {
+    const int q = t % 5;
+    const int j = (t / 5) % NC;
+    const int c = (t / (5 * NC)) % MAXCPL;
+    const int lg = t / (5 * NC * MAXCPL);
+    const int i = blockIdx.y * mp.G * mp.cpl + lg + c * mp.G;
+    if (c < mp.cpl && i < a.m0 && sred[t] != 0.0) atomicAdd(&a.acc[5 * (i * NC + j) + q], sred[t]);
+  }
+  __threadfence();
+  __syncthreads();
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    const unsigned tot = gridDim.x * gridDim.y;
+    s_last = (atomicAdd(&a.ctl->ticket, 1u) == tot - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    cocg_scalar_step<T>(a, NC);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// COCG update kernel
+// ---------------------------------------------------------------------------
+template <typename T, int NC, int MAXCPL>
+__global__ void __launch_bounds__(THREADS) k_cocg_update(CocgArgs<T> a, int buf) {
+  using C = c2<T>;
+  if (__ldcg(&a.ctl->done)) return;
+  const RowMap mp = row_map(a.lanes, a.cpl);
+  const int ibase = blockIdx.y * mp.G * mp.cpl + mp.lg;
+  const T* __restrict__ R = a.r[buf];
+  const T* __restrict__ P = a.p[buf];
+  T* __restrict__ Rn = a.r[buf ^ 1];
+  T* __restrict__ Pn = a.p[buf ^ 1];
+  const int64_t ldt = (int64_t)a.ldc * 2;
+  const C* zs = reinterpret_cast<const C*>(a.zs);
+  C zv[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) zv[j] = zs[j];
+  // stage this block's coefficients in shared memory
+  extern __shared__ unsigned char smem_raw[];
+  Coef<T>* scf = reinterpret_cast<Coef<T>*>(smem_raw);
+  const int i0 = blockIdx.y * mp.G * mp.cpl;
+  const int ncols = min(mp.G * mp.cpl, a.m0 - i0);
+  for (int t = threadIdx.x; t < ncols * NC; t += blockDim.x) scf[t] = a.cf[i0 * NC + t];
+  __syncthreads();
+  int coff[MAXCPL];
+  unsigned mask = 0;
+#pragma unroll
+  for (int c = 0; c < MAXCPL; ++c) {
+    const int i = ibase + c * mp.G;
+    coff[c] = i * NC * 2;
+    if (c < mp.cpl && i < a.m0 && __ldcg(a.colact + i)) mask |= 1u << c;
+  }
+  if (!mask) return;
+  for (int64_t row = mp.gid; row < a.n; row += mp.gstride) {
+    const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
+    C ar[MAXCPL][NC], ap[MAXCPL][NC];
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+#pragma unroll
+      for (int j = 0; j < NC; ++j) ar[c][j] = ap[c][j] = mk<T>((T)0, (T)0);
+    gather_row2<T, NC, MAXCPL>(a.colidx, a.val, k0, k1, R, P, ldt, coff, mask, ar, ap);
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+      if (mask & (1u << c)) {
+        C rv[NC], pv[NC];
+        ld_chunk<NC>(R + row * ldt + coff[c], rv);
+        ld_chunk<NC>(P + row * ldt + coff[c], pv);
+        const int il = (ibase + c * mp.G) - i0;
+        T dsum = (T)0;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          const Coef<T> cf = scf[il * NC + j];
+          // p_k = ar r_k + beta p_{k-1};  L p_k from the gathered sums
+          const C pn = cfma<T>(cf.beta, pv[j], mk<T>(cf.ar * rv[j].x, cf.ar * rv[j].y));
+          const C lpn = cfma<T>(cf.beta, ap[c][j], mk<T>(cf.ar * ar[c][j].x, cf.ar * ar[c][j].y));
+          const C s = csub<T>(cmul<T>(zv[j], pn), lpn);
+          rv[j] = csub<T>(rv[j], cmul<T>(cf.alpha, s));
+          pv[j] = pn;
+          dsum = fma(cf.ca.x, pn.x, fma(-cf.ca.y, pn.y, dsum));
+        }
+        st_chunk<NC>(Rn + row * ldt + coff[c], rv);
+        st_chunk<NC>(Pn + row * ldt + coff[c], pv);
+        T* dp = a.dacc + row * a.ldd + (ibase + c * mp.G);
+        *dp += dsum;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// plain SpMM variants
+// ---------------------------------------------------------------------------
+template <typename T, int NC, int MAXCPL>
+__global__ void __launch_bounds__(THREADS) k_shifted_spmm(int64_t n, const int32_t* rp,
+                                                          const int32_t* ci, const T* val,
+                                                          int m, int ldc, const void* zsp,
+                                                          const T* P, T* W, int G, int cpl) {
+  using C = c2<T>;
+  const RowMap mp = row_map(G, cpl);
+  const int ibase = blockIdx.y * G * cpl + mp.lg;
+  const int64_t ldt = (int64_t)ldc * 2;
+  const C* zs = reinterpret_cast<const C*>(zsp);
+  C zv[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) zv[j] = zs[j];
+  int coff[MAXCPL];
+  unsigned mask = 0;
+#pragma unroll
+  for (int c = 0; c < MAXCPL; ++c) {
+    const int i = ibase + c * G;
+    coff[c] = i * NC * 2;
+    if (c < cpl && i < m) mask |= 1u << c;
+  }
+  if (!mask) return;
+  for (int64_t row = mp.gid; row < n; row += mp.gstride) {
+    C acc[MAXCPL][NC];
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[c][j] = mk<T>((T)0, (T)0);
+    gather_row<T, NC, MAXCPL>(ci, val, __ldg(rp + row), __ldg(rp + row + 1), P, ldt, coff, mask, acc);
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+      if (mask & (1u << c)) {
+        C pv[NC];
+        ld_chunk<NC>(P + row * ldt + coff[c], pv);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) pv[j] = csub<T>(cmul<T>(zv[j], pv[j]), acc[c][j]);
+        st_chunk<NC>(W + row * ldt + coff[c], pv);
+      }
+  }
+}
+
+template <typename T, int MAXCPL>
+__global__ void __launch_bounds__(THREADS) k_spmm_real(int64_t n, const int32_t* rp,
+                                                       const int32_t* ci, const T* val, int mc,
+                                                       int ld, T sL, T sI, const T* X, T* Y,
+                                                       int G, int cpl) {
+  using C = c2<T>;
+  const RowMap mp = row_map(G, cpl);
+  const int ibase = blockIdx.y * G * cpl + mp.lg;
+  int coff[MAXCPL];
+  unsigned mask = 0;
+#pragma unroll
+  for (int c = 0; c < MAXCPL; ++c) {
+    const int i = ibase + c * G;
+    coff[c] = i * 2;
+    if (c < cpl && i < mc) mask |= 1u << c;
+  }
+  if (!mask) return;
+  for (int64_t row = mp.gid; row < n; row += mp.gstride) {
+    C acc[MAXCPL][1];
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c) acc[c][0] = mk<T>((T)0, (T)0);
+    gather_row<T, 1, MAXCPL>(ci, val, __ldg(rp + row), __ldg(rp + row + 1), X, ld, coff, mask, acc);
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+      if (mask & (1u << c)) {
+        C xv[1];
+        ld_chunk<1>(X + row * ld + coff[c], xv);
+        C y = mk<T>(sL * acc[c][0].x + sI * xv[0].x, sL * acc[c][0].y + sI * xv[0].y);
+        *reinterpret_cast<C*>(Y + row * ld + coff[c]) = y;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int g_num_sms_cache = 0;
+
+template <typename K>
+static int grid_x(K kernel, size_t smem, int num_sms, int64_t rows_needed_groups) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, THREADS, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  int64_t g = (int64_t)num_sms * occ;
+  if (g > rows_needed_groups) g = rows_needed_groups;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename T, int NC>
+static void dispatch_dots(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
+  constexpr int MC = maxcpl_of<T>(NC);
+  auto kern = k_cocg_dots<T, NC, MC>;
+  const size_t smem = (size_t)a.lanes * MC * NC * 5 * sizeof(double);
+  const int colblocks = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);
+  const int64_t groups = (a.n + (int64_t)WARPS * (32 / a.lanes) - 1) / ((int64_t)WARPS * (32 / a.lanes));
+  dim3 grid(grid_x(kern, smem, num_sms, groups), colblocks);
+  kern<<<grid, THREADS, smem, s>>>(a, buf);
+  RF_LAUNCH();
+}
+
+template <typename T, int NC>
+static void dispatch_update(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
+  constexpr int MC = maxcpl_of<T>(NC);
+  auto kern = k_cocg_update<T, NC, MC>;
+  const size_t smem = (size_t)a.lanes * MC * NC * sizeof(Coef<T>);
+  const int colblocks = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);
+  const int64_t groups = (a.n + (int64_t)WARPS * (32 / a.lanes) - 1) / ((int64_t)WARPS * (32 / a.lanes));
+  dim3 grid(grid_x(kern, smem, num_sms, groups), colblocks);
+  kern<<<grid, THREADS, smem, s>>>(a, buf);
+  RF_LAUNCH();
+}
+
+template <typename T>
+void launch_cocg_init(const CocgArgs<T>& a, int NC, int num_sms, cudaStream_t s) {
+  k_cocg_reset<T><<<(a.m0 * NC + 255) / 256, 256, 0, s>>>(a, NC);
+  RF_LAUNCH();
+  const int64_t total = a.n * (int64_t)a.m0;
+  int64_t blocks = (total + THREADS - 1) / THREADS;
+  if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
+  if (blocks < 1) blocks = 1;
+  switch (NC) {
+    case 1: k_cocg_init<T, 1><<<(int)blocks, THREADS, 0, s>>>(a); break;
+    case 2: k_cocg_init<T, 2><<<(int)blocks, THREADS, 0, s>>>(a); break;
+    case 4: k_cocg_init<T, 4><<<(int)blocks, THREADS, 0, s>>>(a); break;
+    case 8: k_cocg_init<T, 8><<<(int)blocks, THREADS, 0, s>>>(a); break;
+    default: throw Err{RAFEAST_ERR_INVALID_ARG};
+  }
+  RF_LAUNCH();
+}
+
+template <typename T>
+void launch_cocg_dots(const CocgArgs<T>& a, int NC, int buf, int num_sms, cudaStream_t s) {
+  switch (NC) {
+    case 1: dispatch_dots<T, 1>(a, buf, num_sms, s); break;
+    case 2: dispatch_dots<T, 2>(a, buf, num_sms, s); break;
+    case 4: dispatch_dots<T, 4>(a, buf, num_sms, s); break;
+    case 8: dispatch_dots<T, 8>(a, buf, num_sms, s); break;
+    default: throw Err{RAFEAST_ERR_INVALID_ARG};
+  }
+}
+
+template <typename T>
+void launch_cocg_update(const CocgArgs<T>& a, int NC, int buf, int num_sms, cudaStream_t s) {
+  switch (NC) {
+    case 1: dispatch_update<T, 1>(a, buf, num_sms, s); break;
+    case 2: dispatch_update<T, 2>(a, buf, num_sms, s); break;
+    case 4: dispatch_update<T, 4>(a, buf, num_sms, s); break;
+    case 8: dispatch_update<T, 8>(a, buf, num_sms, s); break;
+    default: throw Err{RAFEAST_ERR_INVALID_ARG};
+  }
+}
+
+template <typename T, int NC>
+static void dispatch_shifted(int64_t n, const int32_t* rp, const int32_t* ci, const T* val, int m,
+                             int ldc, const void* zs, const T* P, T* W, int G, int cpl,
+                             int num_sms, cudaStream_t s) {
+  constexpr int MC = maxcpl_of<T>(NC);
+  if (cpl > MC) throw Err{RAFEAST_ERR_INVALID_ARG};
+  auto kern = k_shifted_spmm<T, NC, MC>;
+  const int colblocks = (m + G * cpl - 1) / (G * cpl);
+  const int64_t groups = (n + (int64_t)WARPS * (32 / G) - 1) / ((int64_t)WARPS * (32 / G));
+  dim3 grid(grid_x(kern, 0, num_sms, groups), colblocks);
+  kern<<<grid, THREADS, 0, s>>>(n, rp, ci, val, m, ldc, zs, P, W, G, cpl);
+  RF_LAUNCH();
+}
+
+template <typename T>
+void launch_shifted_spmm(int64_t n, const int32_t* rp, const int32_t* ci, const T* val, int m,
+                         int ldc, int NC, const void* zs, const T* P, T* W, int lanes, int cpl,
+                         int num_sms, cudaStream_t s) {
+  switch (NC) {
+    case 1: dispatch_shifted<T, 1>(n, rp, ci, val, m, ldc, zs, P, W, lanes, cpl, num_sms, s); break;
+    case 2: dispatch_shifted<T, 2>(n, rp, ci, val, m, ldc, zs, P, W, lanes, cpl, num_sms, s); break;
+    case 4: dispatch_shifted<T, 4>(n, rp, ci, val, m, ldc, zs, P, W, lanes, cpl, num_sms, s); break;
+    case 8: dispatch_shifted<T, 8>(n, rp, ci, val, m, ldc, zs, P, W, lanes, cpl, num_sms, s); break;
+    default: throw Err{RAFEAST_ERR_INVALID_ARG};
+  }
+}
+
+template <typename T>
+void launch_spmm_real(int64_t n, const int32_t* rp, const int32_t* ci, const T* val, int k,
+                      int ld, double sL, double sI, const T* X, T* Y, int num_sms,
+                      cudaStream_t s) {
+  constexpr int MC = maxcpl_of<T>(1);
+  const int mc = (k + 1) / 2;
+  int G, cpl, blocks;
+  choose_shape(mc, 1, sizeof(T) == 8, 0, G, cpl, blocks);
+  auto kern = k_spmm_real<T, MC>;
+  const int64_t groups = (n + (int64_t)WARPS * (32 / G) - 1) / ((int64_t)WARPS * (32 / G));
+  dim3 grid(grid_x(kern, 0, num_sms, groups), blocks);
+  kern<<<grid, THREADS, 0, s>>>(n, rp, ci, val, mc, ld, (T)sL, (T)sI, X, Y, G, cpl);
+  RF_LAUNCH();
+}
+
+// explicit instantiations
+template void launch_cocg_init<float>(const CocgArgs<float>&, int, int, cudaStream_t);
+template void launch_cocg_init<double>(const CocgArgs<double>&, int, int, cudaStream_t);
+template void launch_cocg_dots<float>(const CocgArgs<float>&, int, int, int, cudaStream_t);
+template void launch_cocg_dots<double>(const CocgArgs<double>&, int, int, int, cudaStream_t);
+template void launch_cocg_update<float>(const CocgArgs<float>&, int, int, int, cudaStream_t);
+template void launch_cocg_update<double>(const CocgArgs<double>&, int, int, int, cudaStream_t);
+template void launch_shifted_spmm<float>(int64_t, const int32_t*, const int32_t*, const float*, int,
+                                         int, int, const void*, const float*, float*, int, int,
+                                         int, cudaStream_t);
+template void launch_shifted_spmm<double>(int64_t, const int32_t*, const int32_t*, const double*,
+                                          int, int, int, const void*, const double*, double*, int,
+                                          int, int, cudaStream_t);
+template void launch_spmm_real<float>(int64_t, const int32_t*, const int32_t*, const float*, int,
+                                      int, double, double, const float*, float*, int,
+                                      cudaStream_t);
+template void launch_spmm_real<double>(int64_t, const int32_t*, const int32_t*, const double*, int,
+                                       int, double, double, const double*, double*, int,
+                                       cudaStream_t);
+
+}  // namespace rafeast

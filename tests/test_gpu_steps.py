@@ -1,0 +1,216 @@
+"""Step-level parity of the CUDA path against the oracle (one test group per
+hot-path step): Omega generator, SpMM variants, Cholesky-QR, Rayleigh-Ritz,
+residuals, the batched-COCG quadrature filter. Sizes span several tiles and
+a ragged tail; matrices include empty rows and a dense row."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from gpu_util import colmajor_dev, from_colmajor, rand_sym_csr, to_dev
+from oracle import exact as E
+from oracle import feast as OF
+from oracle import metrics as M
+from oracle import philox as OP
+from oracle import quadrature as OQ
+from workloads import graphs as G
+
+pytestmark = pytest.mark.gpu
+
+
+# ---- a2: Omega ----------------------------------------------------------------
+
+def test_philox_words_bit_exact(lib):
+    import torch
+    for first, nb in [(0, 1000), (123456789, 77)]:
+        words = torch.zeros(4 * nb, dtype=torch.int64, device="cuda")
+        lib.rafeast_philox(2**40 + 3, first, nb, words)
+        got = words.cpu().numpy().view(np.uint64).reshape(nb, 4)
+        exp = OP.philox_blocks(np.arange(first, first + nb, dtype=np.uint64), 2**40 + 3)
+        assert np.array_equal(got, exp)
+
+
+@pytest.mark.parametrize("flags", [0, 2])
+def test_omega_matches_oracle(lib, flags):
+    import torch
+    lap = G.grid2d(7, 9)  # n = 63: n*k not a multiple of 4
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, 0.0, flags=flags)
+    try:
+        for k in [1, 5, 12]:
+            om = torch.zeros((k, lap.n), dtype=torch.float64, device="cuda")
+            lib.rafeast_draw_omega(h, 99, k, om)
+            exp = OP.gaussian_matrix(lap.n, k, 99)
+            assert np.abs(from_colmajor(om) - exp).max() < 1e-13
+    finally:
+        lib.rafeast_destroy(h)
+
+
+# ---- a5: SpMM -----------------------------------------------------------------
+
+@pytest.mark.parametrize("flags", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 7, 24, 65, 130])
+def test_spmm_real(lib, flags, k):
+    import torch
+    n = 1531
+    rp, ci, va, a = rand_sym_csr(n, 3)
+    shift = 0.37
+    h = lib.rafeast_create(rp, ci, va, shift, flags=flags)
+    try:
+        rng = np.random.default_rng(k)
+        x = rng.standard_normal((n, k))
+        X = colmajor_dev(x)
+        Y = torch.zeros_like(X)
+        alpha, beta = -0.7, 1.3
+        lib.rafeast_spmm(h, k, alpha, beta, X, Y, lib.RAFEAST_FP64)
+        A = (a + shift * sp.identity(n)).tocsr()
+        exp = alpha * (A @ x) + beta * x
+        assert np.abs(from_colmajor(Y) - exp).max() <= 1e-13 * np.abs(exp).max()
+        # float32 kernel: inputs rounded to float32, float32 accumulation
+        lib.rafeast_spmm(h, k, alpha, beta, X, Y, lib.RAFEAST_MIXED)
+        x32 = x.astype(np.float32).astype(np.float64)
+        a32 = a.copy()
+        a32.data = a32.data.astype(np.float32).astype(np.float64)
+        exp32 = alpha * (a32 @ x32 + shift * x32) + beta * x32
+        err = np.abs(from_colmajor(Y) - exp32).max() / np.abs(exp32).max()
+        assert err < 2e-6
+    finally:
+        lib.rafeast_destroy(h)
+
+
+def _pack(Pc):
+    """complex (m, nc, n) -> float64 (m, nc, n, 2) (entry (i, col, j))."""
+    out = np.empty(Pc.shape + (2,))
+    out[..., 0] = Pc.real
+    out[..., 1] = Pc.imag
+    return out
+
+
+@pytest.mark.parametrize("nc", [1, 2, 3, 4, 5, 8])
+@pytest.mark.parametrize("m", [1, 9, 40])
+def test_shifted_spmm(lib, nc, m):
+    import torch
+    lap = G.knn3d(900, 6, seed=5, shift=1e-3)
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    try:
+        n = lap.n
+        rng = np.random.default_rng(nc * 100 + m)
+        z = rng.uniform(0, 2, nc) + 1j * rng.uniform(0.01, 1, nc)
+        Pc = rng.standard_normal((m, nc, n)) + 1j * rng.standard_normal((m, nc, n))
+        P = to_dev(_pack(Pc))
+        W = torch.zeros_like(P)
+        A = lap.scipy()
+        exp = np.empty_like(Pc)
+        for col in range(m):
+            for j in range(nc):
+                exp[col, j] = z[j] * Pc[col, j] - A @ Pc[col, j]
+        for prec, tol in [(lib.RAFEAST_FP64, 1e-13), (lib.RAFEAST_MIXED, 3e-6)]:
+            lib.rafeast_shifted_spmm(h, nc, z, m, P, W, prec)
+            got = W.cpu().numpy()
+            got = got[..., 0] + 1j * got[..., 1]
+            assert np.abs(got - exp).max() <= tol * np.abs(exp).max()
+    finally:
+        lib.rafeast_destroy(h)
+
+
+# ---- a8: Cholesky-QR -------------------------------------------------------------
+
+@pytest.mark.parametrize("m,cond", [(1, 1.0), (17, 1e2), (40, 1e6), (96, 1e3), (64, 1e12)])
+def test_orthonormalize(lib, m, cond):
+    n = 2411
+    lap = G.path(n)  # only the handle's n and row order matter here
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, 0.0, flags=2)
+    try:
+        rng = np.random.default_rng(m)
+        u, _ = np.linalg.qr(rng.standard_normal((n, m)))
+        v, _ = np.linalg.qr(rng.standard_normal((m, m)))
+        s = np.logspace(0, -np.log10(cond), m)
+        x = (u * s) @ v.T
+        Q = colmajor_dev(x)
+        R = lib.rafeast_orthonormalize(h, m, Q, want_r=True)
+        q = from_colmajor(Q)
+        assert M.orth_err(q) < 1e-12
+        assert np.allclose(np.tril(R, -1), 0.0)
+        assert np.linalg.norm(q @ R - x) <= 1e-12 * np.linalg.norm(x) * max(1.0, cond * 1e-4)
+        if cond <= 1e6:
+            assert M.sin_theta(q, u) < 1e-9 * cond
+    finally:
+        lib.rafeast_destroy(h)
+
+
+# ---- a9/a10: Rayleigh-Ritz and residuals -----------------------------------------
+
+@pytest.mark.parametrize("m", [1, 6, 31, 80, 116])
+def test_rayleigh_ritz(lib, m):
+    lap = G.knn3d(1800, 8, seed=11, shift=1e-3)
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    try:
+        a = lap.scipy()
+        q0 = OF.random_start(lap.n, m, 4)
+        Q = colmajor_dev(q0)
+        theta, res = lib.rafeast_rayleigh_ritz(h, m, Q)
+        lam, qv, aqv = OF.rayleigh_ritz(a, q0)
+        assert np.abs(theta - lam).max() <= 1e-12 * np.abs(lam).max()
+        q = from_colmajor(Q)
+        # same Ritz vectors up to sign where Ritz values are separated
+        gap = np.min(np.diff(lam)) if m > 1 else 1.0
+        if gap > 1e-6:
+            d = np.abs(np.sum(q * qv, axis=0))
+            assert np.all(np.abs(d - 1.0) < 1e-8)
+        assert M.orth_err(q) < 1e-12
+        ores = OF.residuals(a, theta, q)
+        assert np.allclose(res, ores, rtol=1e-8, atol=1e-15)
+    finally:
+        lib.rafeast_destroy(h)
+
+
+# ---- a1 + a4..a7: the quadrature filter (batched COCG) ---------------------------
+
+def _filter_case():
+    dims = (14, 17)
+    lap = G.grid2d(*dims, shift=0.0)
+    vals, _ = E.grid_spectrum(dims)
+    lmin, lmax = 0.5 * (vals[1] + vals[2]), 0.5 * (vals[8] + vals[9])
+    return lap, lmin, lmax
+
+
+@pytest.mark.parametrize("form", ["direct", "correction"])
+@pytest.mark.parametrize("nc,e", [(1, 1.0), (2, 1.0), (3, 0.5), (4, 1.0), (5, 0.3), (8, 1.0)])
+def test_filter_fp64(lib, form, nc, e):
+    import torch
+    lap, lmin, lmax = _filter_case()
+    m0 = 11
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    try:
+        q0 = OF.random_start(lap.n, m0, 3)
+        z, w = OQ.nodes(lmin, lmax, nc, e)
+        exp, stats = OF.filter_apply(lap.scipy(), q0, z, w, 1e-13, 4000, form)
+        Qt = torch.zeros((m0, lap.n), dtype=torch.float64, device="cuda")
+        fm = lib.RAFEAST_FORM_DIRECT if form == "direct" else lib.RAFEAST_FORM_CORRECTION
+        prm = lib.make_params(lmin, lmax, m0, nc, e, 1e-13, 1e-10, 1, 4000, lib.RAFEAST_FP64, fm)
+        info = lib.rafeast_filter(h, prm, colmajor_dev(q0), None, Qt)
+        got = from_colmajor(Qt)
+        assert np.linalg.norm(got - exp) <= 1e-10 * np.linalg.norm(exp)
+        omax = max(int(s.iters.max()) for s in stats)
+        assert abs(info.cocg_max_last - omax) <= 2
+    finally:
+        lib.rafeast_destroy(h)
+
+
+@pytest.mark.parametrize("form", ["direct", "correction"])
+@pytest.mark.parametrize("nc", [2, 4])
+def test_filter_mixed(lib, form, nc):
+    import torch
+    lap, lmin, lmax = _filter_case()
+    m0 = 11
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    try:
+        q0 = OF.random_start(lap.n, m0, 3)
+        z, w = OQ.nodes(lmin, lmax, nc, 1.0)
+        exp, _ = OF.filter_apply(lap.scipy(), q0, z, w, 1e-13, 4000, form)
+        Qt = torch.zeros((m0, lap.n), dtype=torch.float64, device="cuda")
+        fm = lib.RAFEAST_FORM_DIRECT if form == "direct" else lib.RAFEAST_FORM_CORRECTION
+        prm = lib.make_params(lmin, lmax, m0, nc, 1.0, 1e-5, 1e-10, 1, 4000, lib.RAFEAST_MIXED, fm)
+        lib.rafeast_filter(h, prm, colmajor_dev(q0), None, Qt)
+        got = from_colmajor(Qt)
+        assert np.linalg.norm(got - exp) <= 1e-3 * np.linalg.norm(exp)
+    finally:
+        lib.rafeast_destroy(h)

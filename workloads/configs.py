@@ -1,0 +1,116 @@
+"""The five benchmark workloads (seeded synthetic inputs, no method arithmetic).
+
+Each config names the matrix generator, the solver parameters and where its
+search interval comes from. Intervals that need a spectrum pre-pass are read
+from ``tests/golden/spectra.json`` (written by ``tests/golden/make_golden.py``
+with the oracle's exact eigensolvers); the closed-form ones are stored there
+too, so every consumer reads the same numbers.
+
+* ``grid2d``  plain FEAST, FP64: 2-D 5-point grid 40x50 (n=2000, nnz=9820),
+  16 smallest nonzero eigenvalues, m0=24, N_c=8, COCG tol 1e-10, outer 1e-10,
+  random start from seed 0.
+* ``knn8k``   RA-FEAST, FP64: kNN graph, 8000 uniform points in [0,1]^3
+  (seed 1), k=10, union-symmetrised, unit weights, + 1e-3 I; the 32 smallest
+  eigenvalues; p=10, q=2, m0=42, N_c=2, COCG tol 1e-4, outer 1e-10. Compared
+  with plain FEAST at N_c=8, COCG tol 1e-10 on the same matrix.
+* ``knn200k`` RA-FEAST, mixed: the same construction with n=200,000 (seed 2),
+  64 smallest eigenvalues, m0=80, N_c=4, p=20, q=2.
+* ``grid3d``  RA-FEAST, mixed: 3-D 7-point grid 100^3 (n=1e6, nnz=6.94e6)
+  + 1e-2 I, 63 eigenvalues in [0.005, 0.0272568], m0=96, N_c=4, p=20, q=2.
+* ``sbm64``   batched RA-FEAST, mixed: 64 stochastic-block-model Laplacians
+  + 1e-3 I, n log-uniform in [2000, 300000] (seed 4), 4..16 blocks,
+  p_in = 20/n_block, p_out = 1/n, k = blocks + 8, m0 = ceil(1.5 k), N_c=2.
+"""
+from __future__ import annotations
+
+import dataclasses
+import json
+import math
+import os
+
+import numpy as np
+
+from . import graphs
+
+GOLDEN = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "tests", "golden", "spectra.json")
+
+
+@dataclasses.dataclass
+class Config:
+    key: str
+    make: callable          # () -> graphs.Laplacian
+    count: int              # eigenvalues inside the interval
+    m0: int
+    nc: int
+    precision: str          # "fp64" | "mixed"
+    solve_tol: float
+    outer_tol: float
+    form: str               # "direct" | "correction"
+    warmstart: bool
+    p: int = 0
+    q: int = 0
+    seed: int = 0
+    e: float = 1.0
+    max_outer: int = 40
+    max_inner: int = 20000
+    description: str = ""
+
+
+def _cfgs():
+    return {
+        "grid2d": Config("grid2d", lambda: graphs.grid2d(40, 50, 0.0), 16, 24, 8,
+                         "fp64", 1e-10, 1e-10, "direct", False, seed=0,
+                         description="plain FEAST FP64, 2-D grid 40x50"),
+        "knn8k": Config("knn8k", lambda: graphs.knn3d(8000, 10, 1, 1e-3), 32, 42, 2,
+                        "fp64", 1e-4, 1e-10, "correction", True, p=10, q=2, seed=1,
+                        description="RA-FEAST FP64, kNN n=8000"),
+        "knn8k_plain": Config("knn8k_plain", lambda: graphs.knn3d(8000, 10, 1, 1e-3),
+                              32, 42, 8, "fp64", 1e-10, 1e-10, "direct", False,
+                              seed=1, description="plain FEAST FP64 N_c=8, kNN n=8000"),
+        "knn200k": Config("knn200k", lambda: graphs.knn3d(200000, 10, 2, 1e-3), 64, 80, 4,
+                          "mixed", 1e-4, 1e-11, "correction", True, p=20, q=2, seed=2,
+                          description="RA-FEAST mixed, kNN n=200000"),
+        "grid3d": Config("grid3d", lambda: graphs.grid3d(100, 100, 100, 1e-2), 63, 96, 4,
+                         "mixed", 1e-4, 1e-11, "correction", True, p=20, q=2, seed=3,
+                         description="RA-FEAST mixed, 3-D grid 100^3"),
+    }
+
+
+CONFIGS = _cfgs()
+
+
+def sbm_instances(count: int = 64, seed: int = 4, n_lo: int = 2000,
+                  n_hi: int = 300000):
+    """Parameters of the batched SBM sweep: list of dicts with n, blocks,
+    block sizes, p_in, p_out, k, m0 and a per-instance seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        kb = int(rng.integers(4, 17))
+        base = n // kb
+        sizes = [base + (1 if b < n - base * kb else 0) for b in range(kb)]
+        nb = n / kb
+        k = kb + 8
+        out.append(dict(index=t, n=n, blocks=kb, sizes=sizes, p_in=20.0 / nb,
+                        p_out=1.0 / n, k=k, m0=int(math.ceil(1.5 * k)),
+                        seed=seed * 1000 + t))
+    return out
+
+
+def make_sbm(inst) -> graphs.Laplacian:
+    return graphs.sbm(inst["sizes"], inst["p_in"], inst["p_out"], inst["seed"], 1e-3)
+
+
+def load_golden():
+    if not os.path.exists(GOLDEN):
+        raise FileNotFoundError(f"missing {GOLDEN}; run tests/golden/make_golden.py")
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def interval(key: str):
+    """(lmin, lmax) of a config from the stored spectrum pre-pass."""
+    g = load_golden()[key]
+    return g["lmin"], g["lmax"]
