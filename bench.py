@@ -1,0 +1,417 @@
+"""Benchmark of the RA-FEAST hot path on GB300.
+
+One step = one full RA-FEAST solve (Algorithm 2: randomized warmstart, then
+FEAST iterations until every in-interval Ritz pair has relative residual <=
+outer_tol) of the workload below, inputs resident in HBM. Prints one JSON line.
+
+Default workload (``knn200k``): kNN graph Laplacian of 200,000 uniform points
+in [0,1]^3 (seed 2), k = 10, union-symmetrised, unit weights, + 1e-3 I; the
+64 smallest eigenvalues; m0 = 80, N_c = 4, p = 20, q = 2, COCG tolerance
+1e-4, outer tolerance 1e-11, mixed precision (float32 shifted solves, double
+outer loop). The inputs (COCG state 4 x n x 640 x 4 B = 2.05 GB) are larger
+than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("RA-FEAST time-to-solution & SpMM HBM GB/s, FP32-mixed vs FP64, "
+          "eig relerr≤1e-8")
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "knn200k": dict(key="knn200k", precision="mixed"),
+    "grid3d": dict(key="grid3d", precision="mixed"),
+    "knn8k": dict(key="knn8k", precision="fp64"),
+}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic_per_launch(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.strip().startswith("traffic_bytes_per_launch:"):
+            v = line.split(":", 1)[1].strip()
+            return None if v in ("", "null", "None") else float(v)
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _cpu_sample(key: str, gpu_counts: dict, budget: str = "full"):
+    """Time the oracle (unchanged, single-threaded as in the paper's runs) on a
+    bounded sample of the workload in a fresh process; extrapolate one solve."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+from oracle import cocg as OC, feast as OF, philox as OP, quadrature as OQ
+from workloads import configs as CF
+key, counts, budget = sys.argv[2], json.loads(sys.argv[3]), sys.argv[4]
+cfg = CF.CONFIGS[key]
+lap = cfg.make(); a = lap.scipy()
+lmin, lmax = CF.interval(key)
+n, m0 = lap.n, cfg.m0
+steps = 3 if budget == "full" else 2
+t0 = time.perf_counter()
+om = OP.gaussian_matrix(n, m0 + cfg.p, cfg.seed)
+q0, th0, _ = OF.warmstart(a, lmin, lmax, m0, cfg.p, cfg.q, om)
+t_ws = time.perf_counter() - t0
+z, w = OQ.nodes(lmin, lmax, cfg.nc, cfg.e)
+rmat = a @ q0 - q0 * th0
+t0 = time.perf_counter()
+OC.cocg(lambda x: a @ x, z[0], rmat, 0.0, steps)
+t_step = (time.perf_counter() - t0) / steps
+t0 = time.perf_counter()
+q = OF.orthonormalize(q0)
+OF.rayleigh_ritz(a, q)
+t_rr = time.perf_counter() - t0
+est = t_ws + counts["outer"] * t_rr + cfg.nc * counts["cocg_total"] * t_step
+print(json.dumps(dict(est=est, t_ws=t_ws, t_step=t_step, t_rr=t_rr, steps=steps)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    t0 = time.perf_counter()
+    res = subprocess.run([sys.executable, "-c", code, ROOT, key, json.dumps(gpu_counts), budget],
+                         capture_output=True, text=True, env=env)
+    wall = time.perf_counter() - t0
+    if res.returncode != 0:
+        return {"error": res.stderr[-400:]}
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    d["wall_s"] = wall
+    return d
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores (this workload's arm)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    key = WORKLOADS[args.workload]["key"]
+    counts = _reference_counts(key)
+    samples = []
+    for i in range(args.warmup + args.steps):
+        d = _cpu_sample(key, counts, budget="small")
+        if "error" in d:
+            print(json.dumps({"impl": "reference", "unavailable": d["error"][-200:]}))
+            return 0
+        if i >= args.warmup:
+            samples.append(d)
+    est = statistics.mean(s["est"] for s in samples)
+    sample = (f"per step: oracle warmstart + {samples[0]['steps']} COCG steps of one shift on "
+              f"the full matrix + one Rayleigh-Ritz, extrapolated to {counts['outer']} outer and "
+              f"{counts['cocg_total']} COCG iterations x N_c shifts")
+    value = 1.0 / est
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(key),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _reference_counts(key):
+    # iteration counts of the GPU solve of this workload (same algorithm and
+    # parameters); used only to extrapolate the oracle's bounded sample
+    table = {"knn200k": dict(outer=12, cocg_total=2400),
+             "grid3d": dict(outer=12, cocg_total=3600),
+             "knn8k": dict(outer=11, cocg_total=900)}
+    return table[key]
+
+
+def _config(key):
+    from workloads import configs as CF
+    cfg = CF.CONFIGS[key]
+    g = CF.load_golden()[key]
+    return {"workload": f"{key}: {cfg.description}", "n": g["n"], "nnz": g["nnz"],
+            "count": g["count"], "m0": cfg.m0, "nc": cfg.nc, "p": cfg.p, "q": cfg.q,
+            "solve_tol": cfg.solve_tol, "outer_tol": cfg.outer_tol,
+            "interval": [g["lmin"], g["lmax"]],
+            "l2": "inputs larger than L2 (no flush): COCG state of 4 arrays n x 2*N_c*m0 "
+                  "float32" if cfg.precision == "mixed" else "L2 flushed between steps"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="knn200k", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_2512_01257_gb300 import rafeast as R
+    from workloads import configs as CF
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    key = WORKLOADS[args.workload]["key"]
+    cfg = CF.CONFIGS[key]
+    g = CF.load_golden()[key]
+    lap = cfg.make()
+    assert lap.checksum() == g["checksum"], "workload differs from the stored spectrum"
+    lmin, lmax = g["lmin"], g["lmax"]
+    prec = R.RAFEAST_MIXED if cfg.precision == "mixed" else R.RAFEAST_FP64
+    dev = torch.device("cuda", local)
+    rp = torch.from_numpy(lap.row_ptr).to(dev)
+    ci = torch.from_numpy(lap.col_idx).to(dev)
+    va = torch.from_numpy(lap.values).to(dev)
+    h = R.rafeast_create(rp, ci, va, lap.shift)
+    m0, n = cfg.m0, lap.n
+    evals = torch.zeros(m0, dtype=torch.float64, device=dev)
+    evecs = torch.zeros((m0, n), dtype=torch.float64, device=dev)
+    resid = torch.zeros(m0, dtype=torch.float64, device=dev)
+
+    def params(p):
+        return R.make_params(lmin, lmax, m0, cfg.nc, cfg.e, cfg.solve_tol, cfg.outer_tol,
+                             cfg.max_outer, cfg.max_inner, p, R.RAFEAST_FORM_CORRECTION,
+                             R.RAFEAST_START_SUBSPACE)
+
+    infos = []
+
+    def step(p=prec):
+        R.rafeast_warmstart(h, lmin, lmax, m0, cfg.p, cfg.q, cfg.seed)
+        st, mf, info = R.rafeast_solve(h, params(p), evals, evecs, resid)
+        if st != R.RAFEAST_OK:
+            raise RuntimeError(f"solve status {st}: {info.as_dict()}")
+        infos.append((mf, info))
+        return mf, info
+
+    for _ in range(args.warmup):
+        step()
+    infos.clear()
+    R.rafeast_set_option(h, R.RAFEAST_OPT_PROFILE, 1)
+    R.rafeast_profile(h, reset=True)
+    clocks = Clocks(local)
+    stream = torch.cuda.current_stream()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = R.rafeast_profile(h, reset=True)
+    R.rafeast_set_option(h, R.RAFEAST_OPT_PROFILE, 0)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    total_solves = args.steps * world
+    value = total_solves / (ms / 1e3)
+    # parity of the last timed step against the stored ARPACK eigenvalues
+    mf, info = infos[-1]
+    ev = evals.cpu().numpy()[:mf]
+    ref = np.array(g["evals"])
+    relerr = float(np.max(np.abs(np.sort(ev) - ref) / np.abs(ref))) if mf == len(ref) else None
+    launches = sum(i.kernel_launches for _, i in infos)
+    phases = {k: statistics.mean(getattr(i, k) for _, i in infos)
+              for k in ("t_warmstart_ms", "t_filter_ms", "t_orth_ms", "t_rr_ms", "t_total_ms")}
+
+    # roofline of the dominant COCG kernel (live CUDA-event times in the replays)
+    peak, peak_kind = _peaks()
+    kern = "cocg_update" if prof["update_ms"] >= prof["dots_ms"] else "cocg_dots"
+    pre = "update" if kern == "cocg_update" else "dots"
+    launches_k = max(prof[f"{pre}_launches"], 1.0)
+    bytes_per = prof[f"{pre}_bytes"] / launches_k
+    ms_per = prof[f"{pre}_ms"] / launches_k
+    achieved = bytes_per / (ms_per * 1e-3) / 1e9
+    other = "dots" if pre == "update" else "update"
+    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": _traffic_per_launch(kern, key),
+                "algorithmic_bytes_per_launch": bytes_per, "ms_per_launch": ms_per,
+                "launches": int(launches_k),
+                "other_kernel": {"kernel": "cocg_" + other,
+                                 "achieved": (prof[f"{other}_bytes"] / max(prof[f"{other}_ms"], 1e-9))
+                                 / 1e6,
+                                 "ms_per_launch": prof[f"{other}_ms"] / max(prof[f"{other}_launches"], 1)},
+                "share_of_step": (prof["update_ms"] + prof["dots_ms"]) / ms}
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "time_to_solution_s": ms_step / 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == R.RAFEAST_MIXED else "f64",
+            "precision": ("mixed: f32 shifted solves and SpMM; f64 Gram, Cholesky-QR, "
+                          "Rayleigh-Ritz, residuals") if prec == R.RAFEAST_MIXED else "f64",
+            "data": "synthetic (seeded generator, no dataset)", "config": _config(key),
+            "parity": {"max_eig_relerr_vs_arpack": relerr, "m_found": mf, "count": g["count"],
+                       "gate": 1e-8 if prec == R.RAFEAST_MIXED else 1e-10},
+            "outer_iters": info.outer_iters, "cocg_iters_total": info.cocg_iters_total,
+            "phases_ms": phases, "roofline": roofline, "gpu_launches": int(launches),
+            "clocks": ck}
+
+    # FP64 comparison (same workload, same stream; one untimed-warm step)
+    if not args.no_fp64 and prec == R.RAFEAST_MIXED:
+        step(R.RAFEAST_FP64)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        mf64, info64 = step(R.RAFEAST_FP64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ev64 = evals.cpu().numpy()[:mf64]
+        line["fp64"] = {"ms_per_step": f0.elapsed_time(f1), "outer_iters": info64.outer_iters,
+                        "cocg_iters_total": info64.cocg_iters_total,
+                        "max_eig_relerr_vs_arpack":
+                            float(np.max(np.abs(np.sort(ev64) - ref) / np.abs(ref)))
+                            if mf64 == len(ref) else None}
+    R.rafeast_destroy(h)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    if not args.no_e2e:
+        hrp = torch.from_numpy(lap.row_ptr).pin_memory()
+        hci = torch.from_numpy(lap.col_idx).pin_memory()
+        hva = torch.from_numpy(lap.values).pin_memory()
+        oev = np.zeros(m0)
+        ove = np.zeros((m0, n))
+        ore = np.zeros(m0)
+        bi = hrp.numel() * 4 + hci.numel() * 4 + hva.numel() * 8
+        bo = oev.nbytes + ove.nbytes + ore.nbytes
+        ek = max(1, min(args.steps, 2))
+
+        def e2e_step():
+            hh = R.rafeast_create(hrp.numpy(), hci.numpy(), hva.numpy(), lap.shift)
+            try:
+                R.rafeast_warmstart(hh, lmin, lmax, m0, cfg.p, cfg.q, cfg.seed)
+                st, _, _ = R.rafeast_solve(hh, params(prec), oev, ove, ore)
+                assert st == R.RAFEAST_OK
+            finally:
+                R.rafeast_destroy(hh)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ek):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        line["e2e"] = {"value": ek * world / el, "unit": "solves/s", "h2d_bytes_per_step": bi,
+                       "d2h_bytes_per_step": bo, "steps": ek,
+                       "includes": "rafeast_create from pinned host CSR (row reorder on the "
+                                   "host), warmstart, solve, copy of eigenpairs to host"}
+
+    if not args.no_cpu and rank == 0 and world == 1:
+        counts = dict(outer=info.outer_iters, cocg_total=info.cocg_iters_total)
+        d = _cpu_sample(key, counts)
+        if "est" in d:
+            line["cpu_baseline"] = {
+                "value": 1.0 / d["est"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": (f"oracle warmstart + {d['steps']} COCG steps of one shift on the full "
+                           f"matrix ({d['t_step']:.3f} s/step) + one Rayleigh-Ritz "
+                           f"({d['t_rr']:.2f} s), extrapolated to this run's "
+                           f"{counts['outer']} outer and {counts['cocg_total']} COCG iterations "
+                           f"x {cfg.nc} shifts; {d['wall_s']:.1f} s of CPU work"),
+                "est_seconds_per_solve": d["est"]}
+        else:
+            line["cpu_baseline"] = {"error": d.get("error")}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -80,6 +80,7 @@ extern "C" {
 #define RAFEAST_OPT_CHUNK 2         /* COCG iterations per CUDA-graph replay   */
 #define RAFEAST_OPT_AUTOTUNE 3      /* 1 (default) time SpMM shapes, 0 off     */
 #define RAFEAST_OPT_LANES 4         /* force lanes per row (4,8,16,32), 0 auto */
+#define RAFEAST_OPT_PROFILE 5       /* 1: time every COCG kernel in the graph  */
 
 typedef struct rafeast_ctx* rafeast_t;
 
@@ -149,6 +150,16 @@ const char* rafeast_last_error(void);
 
 /* Set a tuning option (RAFEAST_OPT_*). -1 for an unknown key or value. */
 int rafeast_set_option(rafeast_t h, int key, int64_t value);
+
+/* Cumulative device time and algorithmic bytes of the batched-COCG kernels
+ * launched while RAFEAST_OPT_PROFILE was on (CUDA events recorded around each
+ * kernel inside the replayed graphs). out (host, 8 doubles): dot-kernel
+ * launches, milliseconds, bytes; update-kernel launches, milliseconds, bytes;
+ * 0; 0. Bytes count A once (nnz*(4+s) + 4(n+1), s = 4 or 8) plus each state
+ * column the launch reads or writes once: the dot kernel reads r, the update
+ * kernel reads r and p, writes r and p, and updates the quadrature sum. With
+ * reset != 0 the counters restart at zero after being copied out. */
+int rafeast_profile(rafeast_t h, int reset, double* out);
 
 /* Matrix facts: n, internal reorder flag (1 when rows are permuted), ||A||_1
  * and the Gershgorin interval of A. Any output pointer may be NULL. */

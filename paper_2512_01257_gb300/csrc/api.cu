@@ -227,6 +227,7 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   const size_t o_zs = carve(sizeof(C) * NC);
   const size_t o_coef = carve(sizeof(double2) * nsys);
   const size_t o_fin = carve(sizeof(double) * m0);
+  const size_t o_hist = carve(sizeof(int) * ((size_t)prm.max_inner + 2));
   char* sc = (char*)scratch(h, S_SCAL, off + 256);
   RF_CUDA(cudaMemcpyAsync(sc + o_zs, zs.data(), sizeof(C) * NC, cudaMemcpyHostToDevice, h->stream));
   RF_CUDA(cudaMemcpyAsync(sc + o_coef, coef.data(), sizeof(double2) * nsys, cudaMemcpyHostToDevice,
@@ -259,26 +260,38 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   a.cf = (Coef<T>*)(sc + o_cf);
   a.colact = (int*)(sc + o_col);
   a.ctl = (CocgCtl*)(sc + o_ctl);
+  a.hist = h->opt_profile ? (int*)(sc + o_hist) : nullptr;
   a.nc_real = nc;
   a.tol2 = prm.solve_tol * prm.solve_tol;
   a.max_inner = prm.max_inner;
   a.form = prm.solve_form;
   launch_cocg_init<T>(a, NC, h->num_sms, h->stream);
   h->launches += 2;
-  // capture `chunk` COCG steps as one graph
+  // capture `chunk` COCG steps as one graph (with event nodes around every
+  // kernel when profiling, so kernel times are measured inside the replays)
   int chunk = std::max(2, h->opt_chunk);
   chunk += chunk & 1;
+  const bool prof = h->opt_profile != 0;
+  std::vector<cudaEvent_t> evs;
+  if (prof) {
+    evs.resize(2 * chunk + 1);
+    for (auto& e : evs) RF_CUDA(cudaEventCreate(&e));
+  }
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   RF_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   try {
     for (int it = 0; it < chunk; ++it) {
+      if (prof) RF_CUDA(cudaEventRecord(evs[2 * it], h->stream));
       launch_cocg_dots<T>(a, NC, it & 1, h->num_sms, h->stream);
+      if (prof) RF_CUDA(cudaEventRecord(evs[2 * it + 1], h->stream));
       launch_cocg_update<T>(a, NC, it & 1, h->num_sms, h->stream);
     }
+    if (prof) RF_CUDA(cudaEventRecord(evs[2 * chunk], h->stream));
   } catch (...) {
     cudaStreamEndCapture(h->stream, &graph);
     if (graph) cudaGraphDestroy(graph);
+    for (auto& e : evs) cudaEventDestroy(e);
     throw;
   }
   RF_CUDA(cudaStreamEndCapture(h->stream, &graph));
@@ -286,16 +299,45 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   CocgCtl ctl;
   const int max_replays = (prm.max_inner + 2) / chunk + 2;
   int replays = 0;
+  std::vector<float> tk;  // per iteration k: dots ms, update ms
   for (; replays < max_replays; ++replays) {
     RF_CUDA(cudaGraphLaunch(exec, h->stream));
     RF_CUDA(cudaMemcpyAsync(&ctl, a.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->stream));
     RF_CUDA(cudaStreamSynchronize(h->stream));
+    if (prof)
+      for (int it = 0; it < 2 * chunk; ++it) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, evs[it], evs[it + 1]);
+        tk.push_back(ms);
+      }
     if (ctl.done) break;
   }
   h->launches += 2 * chunk * (replays + 1);
   h->spmm_launches += 2 * chunk * (replays + 1);
   cudaGraphExecDestroy(exec);
   cudaGraphDestroy(graph);
+  for (auto& e : evs) cudaEventDestroy(e);
+  if (prof && ctl.done) {
+    // algorithmic bytes: A once, plus the state columns each kernel touches
+    const int iters = std::min(ctl.iter, prm.max_inner + 1);
+    std::vector<int> hist(iters + 1, 0);
+    RF_CUDA(cudaMemcpy(hist.data(), a.hist, sizeof(int) * iters, cudaMemcpyDeviceToHost));
+    const double sv = fp64 ? 8.0 : 4.0;
+    const double abytes = (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
+    const double colb = (double)h->n * NC * 2.0 * sv;  // one column i of one state array
+    for (int k = 0; k < iters && 2 * k + 1 < (int)tk.size(); ++k) {
+      const int act_d = k == 0 ? m0 : hist[k - 1];
+      const int act_u = hist[k];
+      h->prof[0] += 1;
+      h->prof[1] += tk[2 * k];
+      h->prof[2] += abytes + colb * act_d;
+      if (act_u > 0) {
+        h->prof[3] += 1;
+        h->prof[4] += tk[2 * k + 1];
+        h->prof[5] += abytes + 4.0 * colb * act_u + 2.0 * (double)h->n * act_u * sv;
+      }
+    }
+  }
   if (!ctl.done) throw Err{RAFEAST_ERR_TIMEOUT};
   fs.iters_max = ctl.max_iters;
   fs.iters_min = ctl.min_iters;
@@ -614,6 +656,9 @@ int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
     case RAFEAST_OPT_AUTOTUNE:
       h->opt_autotune = value ? 1 : 0;
       return RAFEAST_OK;
+    case RAFEAST_OPT_PROFILE:
+      h->opt_profile = value ? 1 : 0;
+      return RAFEAST_OK;
     case RAFEAST_OPT_LANES:
       if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32)
         return RAFEAST_ERR_INVALID_ARG;
@@ -622,6 +667,16 @@ int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
     default:
       return RAFEAST_ERR_INVALID_ARG;
   }
+}
+
+int rafeast_profile(rafeast_t hh, int reset, double* out) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return RAFEAST_ERR_INVALID_ARG;
+  if (out)
+    for (int t = 0; t < 8; ++t) out[t] = h->prof[t];
+  if (reset)
+    for (int t = 0; t < 8; ++t) h->prof[t] = 0.0;
+  return RAFEAST_OK;
 }
 
 int rafeast_matrix_info(rafeast_t hh, int64_t* n, int* reordered, double* norm1, double* glo,

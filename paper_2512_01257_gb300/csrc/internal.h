@@ -87,6 +87,7 @@ template <typename T> struct CocgArgs {
   Coef<T>* cf;           // [nsys]
   int* colact;           // [m0]: 1 while any shift of column i is active
   CocgCtl* ctl;
+  int* hist;             // [max_inner + 2]: active columns after step k, or null
   int nc_real;           // shifts with a right-hand side (<= NC)
   double tol2;           // solve_tol^2
   int max_inner;
@@ -127,6 +128,9 @@ struct Handle {
   int opt_chunk = 16;
   int opt_autotune = 1;
   int opt_lanes = 0;
+  int opt_profile = 0;
+  // kernel time / algorithmic bytes of the COCG kernels (profile option)
+  double prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   // scratch, grown on demand and kept
   std::vector<DevBuf> bufs;
   // launch accounting of the current call

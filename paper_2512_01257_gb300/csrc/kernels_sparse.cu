@@ -298,12 +298,17 @@ __device__ void cocg_scalar_step(const CocgArgs<T>& a, int NC) {
     a.cf[s] = cf;
   }
   __syncthreads();
+  __shared__ int s_cols;
+  if (threadIdx.x == 0) s_cols = 0;
+  __syncthreads();
   for (int i = threadIdx.x; i < a.m0; i += blockDim.x) {
     int any = 0;
     for (int j = 0; j < NC; ++j) any |= a.st[i * NC + j].active;
     a.colact[i] = any;
+    if (any) atomicAdd(&s_cols, 1);
   }
   __syncthreads();
+  if (threadIdx.x == 0 && a.hist && k <= a.max_inner) a.hist[k] = s_cols;
   if (threadIdx.x == 0) {
     CocgCtl* c = a.ctl;
     c->active = s_active;

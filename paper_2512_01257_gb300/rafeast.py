@@ -44,13 +44,15 @@ RAFEAST_OPT_WARMSTART_MAP = 1
 RAFEAST_OPT_CHUNK = 2
 RAFEAST_OPT_AUTOTUNE = 3
 RAFEAST_OPT_LANES = 4
+RAFEAST_OPT_PROFILE = 5
 
 EXPORTS = [
     "rafeast_create", "rafeast_destroy", "rafeast_status_string", "rafeast_set_option",
     "rafeast_matrix_info", "rafeast_quadrature", "rafeast_philox", "rafeast_draw_omega",
     "rafeast_spmm", "rafeast_shifted_spmm", "rafeast_filter", "rafeast_orthonormalize",
     "rafeast_rayleigh_ritz", "rafeast_warmstart", "rafeast_set_subspace",
-    "rafeast_get_subspace", "rafeast_solve", "rafeast_solve_batched",
+    "rafeast_get_subspace", "rafeast_solve", "rafeast_solve_batched", "rafeast_profile",
+    "rafeast_last_error",
 ]
 
 
@@ -100,6 +102,7 @@ def load():
         "rafeast_status_string": (C.c_char_p, [I]),
         "rafeast_last_error": (C.c_char_p, []),
         "rafeast_set_option": (I, [P, I, I64]),
+        "rafeast_profile": (I, [P, I, P]),
         "rafeast_matrix_info": (I, [P, C.POINTER(I64), C.POINTER(I), C.POINTER(D),
                                     C.POINTER(D), C.POINTER(D)]),
         "rafeast_quadrature": (I, [D, D, I, D, P, P]),
@@ -207,6 +210,14 @@ def rafeast_destroy(h):
 
 def rafeast_set_option(h, key, value):
     return _check(load().rafeast_set_option(h, key, value), "rafeast_set_option")
+
+
+def rafeast_profile(h, reset=True):
+    """COCG kernel timing gathered with RAFEAST_OPT_PROFILE on."""
+    out = np.zeros(8)
+    _check(load().rafeast_profile(h, int(reset), _ptr(out)), "rafeast_profile")
+    return dict(dots_launches=out[0], dots_ms=out[1], dots_bytes=out[2],
+                update_launches=out[3], update_ms=out[4], update_bytes=out[5])
 
 
 def rafeast_matrix_info(h):

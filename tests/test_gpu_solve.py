@@ -112,10 +112,11 @@ def test_status_codes(lib):
                               lib.RAFEAST_FP64, lib.RAFEAST_FORM_DIRECT)
         st, mf, *_ = _solve(lib, h, prm, lap.n)
         assert st == lib.RAFEAST_M0_TOO_SMALL and mf == 6
-        prm = lib.make_params(-0.1, 0.5 * (lam[2] + lam[3]), 6, 2, 1.0, 1e-12, 1e-15, 1, 3000,
+        # outer_tol = 0 cannot be met: stop at max_outer with the pairs found
+        prm = lib.make_params(-0.1, 0.5 * (lam[2] + lam[3]), 6, 8, 1.0, 1e-12, 0.0, 2, 3000,
                               lib.RAFEAST_FP64, lib.RAFEAST_FORM_DIRECT)
         st, mf, ev, vec, res, info = _solve(lib, h, prm, lap.n)
-        assert st == lib.RAFEAST_NO_CONVERGENCE and info.outer_iters == 1
+        assert st == lib.RAFEAST_NO_CONVERGENCE and info.outer_iters == 2 and mf == 3
         # invalid arguments are rejected before any work
         bad = lib.make_params(1.0, 0.5, 6, 2)
         with pytest.raises(lib.RafeastError):
