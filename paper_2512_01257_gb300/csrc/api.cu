@@ -25,6 +25,27 @@ void set_last_error(cudaError_t e, const char* what, const char* file, int line)
   snprintf(g_err, sizeof(g_err), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
 }
 
+static int debug_sync() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("RAFEAST_DEBUG_SYNC");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v;
+}
+
+static thread_local bool g_capturing = false;
+
+void check_launch(const char* file, int line) {
+  cudaError_t e = cudaGetLastError();
+  // no device-wide sync while this thread captures a graph
+  if (e == cudaSuccess && debug_sync() && !g_capturing) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    set_last_error(e, "kernel launch", file, line);
+    throw Err{e == cudaErrorMemoryAllocation ? RAFEAST_ERR_OUT_OF_MEMORY : RAFEAST_ERR_CUDA};
+  }
+}
+
 void* scratch(Handle* h, int slot, size_t bytes) {
   if ((int)h->bufs.size() <= slot) h->bufs.resize(slot + 1);
   DevBuf& b = h->bufs[slot];
@@ -46,6 +67,7 @@ struct CallScope {
   explicit CallScope(Handle* hh) : h(hh) {
     h->launches = 0;
     h->spmm_launches = 0;
+    cudaGetLastError();  // a stale error of an earlier call is not ours
     RF_CUDA(cudaSetDevice(h->device));
     RF_CUDA(cudaEventRecord(h->ev_in, h->user_stream));
     RF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
@@ -228,6 +250,7 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   const size_t o_coef = carve(sizeof(double2) * nsys);
   const size_t o_fin = carve(sizeof(double) * m0);
   const size_t o_hist = carve(sizeof(int) * ((size_t)prm.max_inner + 2));
+  const size_t o_rhist = carve(sizeof(double) * ((size_t)prm.max_inner + 2));
   char* sc = (char*)scratch(h, S_SCAL, off + 256);
   RF_CUDA(cudaMemcpyAsync(sc + o_zs, zs.data(), sizeof(C) * NC, cudaMemcpyHostToDevice, h->stream));
   RF_CUDA(cudaMemcpyAsync(sc + o_coef, coef.data(), sizeof(double2) * nsys, cudaMemcpyHostToDevice,
@@ -261,6 +284,7 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   a.colact = (int*)(sc + o_col);
   a.ctl = (CocgCtl*)(sc + o_ctl);
   a.hist = h->opt_profile ? (int*)(sc + o_hist) : nullptr;
+  a.rhist = h->opt_profile ? (double*)(sc + o_rhist) : nullptr;
   a.nc_real = nc;
   a.tol2 = prm.solve_tol * prm.solve_tol;
   a.max_inner = prm.max_inner;
@@ -280,6 +304,7 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   RF_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  g_capturing = true;
   try {
     for (int it = 0; it < chunk; ++it) {
       if (prof) RF_CUDA(cudaEventRecord(evs[2 * it], h->stream));
@@ -289,11 +314,13 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
     }
     if (prof) RF_CUDA(cudaEventRecord(evs[2 * chunk], h->stream));
   } catch (...) {
+    g_capturing = false;
     cudaStreamEndCapture(h->stream, &graph);
     if (graph) cudaGraphDestroy(graph);
     for (auto& e : evs) cudaEventDestroy(e);
     throw;
   }
+  g_capturing = false;
   RF_CUDA(cudaStreamEndCapture(h->stream, &graph));
   RF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
   CocgCtl ctl;
@@ -307,21 +334,25 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
     if (prof)
       for (int it = 0; it < 2 * chunk; ++it) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, evs[it], evs[it + 1]);
+        RF_CUDA(cudaEventElapsedTime(&ms, evs[it], evs[it + 1]));
         tk.push_back(ms);
       }
     if (ctl.done) break;
   }
   h->launches += 2 * chunk * (replays + 1);
   h->spmm_launches += 2 * chunk * (replays + 1);
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
-  for (auto& e : evs) cudaEventDestroy(e);
+  RF_CUDA(cudaGraphExecDestroy(exec));
+  RF_CUDA(cudaGraphDestroy(graph));
+  for (auto& e : evs) RF_CUDA(cudaEventDestroy(e));
   if (prof && ctl.done) {
     // algorithmic bytes: A once, plus the state columns each kernel touches
     const int iters = std::min(ctl.iter, prm.max_inner + 1);
     std::vector<int> hist(iters + 1, 0);
     RF_CUDA(cudaMemcpy(hist.data(), a.hist, sizeof(int) * iters, cudaMemcpyDeviceToHost));
+    h->last_hist.assign(hist.begin(), hist.begin() + iters);
+    h->last_rhist.assign(iters, 0.0);
+    RF_CUDA(cudaMemcpy(h->last_rhist.data(), a.rhist, sizeof(double) * iters,
+                       cudaMemcpyDeviceToHost));
     const double sv = fp64 ? 8.0 : 4.0;
     const double abytes = (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
     const double colb = (double)h->n * NC * 2.0 * sv;  // one column i of one state array
@@ -679,6 +710,17 @@ int rafeast_profile(rafeast_t hh, int reset, double* out) {
   return RAFEAST_OK;
 }
 
+int rafeast_profile_history(rafeast_t hh, int max_len, int* active_cols, double* max_relres) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || max_len < 0) return RAFEAST_ERR_INVALID_ARG;
+  const int len = (int)h->last_hist.size();
+  for (int k = 0; k < std::min(len, max_len); ++k) {
+    if (active_cols) active_cols[k] = h->last_hist[k];
+    if (max_relres) max_relres[k] = h->last_rhist[k];
+  }
+  return len;
+}
+
 int rafeast_matrix_info(rafeast_t hh, int64_t* n, int* reordered, double* norm1, double* glo,
                         double* ghi) {
   Handle* h = reinterpret_cast<Handle*>(hh);
@@ -865,7 +907,7 @@ int rafeast_filter(rafeast_t hh, const rafeast_params* prm, const double* Q, con
   launch_from_internal(h->n, m0, Qti, ldq, Qt, h->perm, nullptr, h->stream);
   RF_CUDA(cudaStreamSynchronize(h->stream));
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
+  RF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (info) {
@@ -1112,9 +1154,9 @@ int rafeast_solve(rafeast_t hh, const rafeast_params* prm, int* m_found, double*
                             cudaMemcpyDeviceToHost, h->stream));
     RF_CUDA(cudaStreamSynchronize(h->stream));
     float a = 0, b = 0, c = 0;
-    cudaEventElapsedTime(&a, ev[2], ev[3]);
-    cudaEventElapsedTime(&b, ev[3], ev[4]);
-    cudaEventElapsedTime(&c, ev[4], ev[5]);
+    RF_CUDA(cudaEventElapsedTime(&a, ev[2], ev[3]));
+    RF_CUDA(cudaEventElapsedTime(&b, ev[3], ev[4]));
+    RF_CUDA(cudaEventElapsedTime(&c, ev[4], ev[5]));
     t_filter += a;
     t_orth += b;
     t_rr += c;
@@ -1168,8 +1210,8 @@ int rafeast_solve(rafeast_t hh, const rafeast_params* prm, int* m_found, double*
   RF_CUDA(cudaEventRecord(ev[5], h->stream));
   RF_CUDA(cudaStreamSynchronize(h->stream));
   float tot = 0, tws = 0;
-  cudaEventElapsedTime(&tot, ev[0], ev[5]);
-  cudaEventElapsedTime(&tws, ev[0], ev[1]);
+  RF_CUDA(cudaEventElapsedTime(&tot, ev[0], ev[5]));
+  RF_CUDA(cudaEventElapsedTime(&tws, ev[0], ev[1]));
   for (auto& e : ev) cudaEventDestroy(e);
   if (info) {
     memset(info, 0, sizeof(*info));

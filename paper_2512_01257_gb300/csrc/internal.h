@@ -26,13 +26,16 @@ struct Err {
                                : RAFEAST_ERR_CUDA};                        \
     }                                                                      \
   } while (0)
-#define RF_LAUNCH() RF_CUDA(cudaGetLastError())
+#define RF_LAUNCH() ::rafeast::check_launch(__FILE__, __LINE__)
 #define RF_CHECK(cond, code)             \
   do {                                   \
     if (!(cond)) throw ::rafeast::Err{code}; \
   } while (0)
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line);
+// after a kernel launch: the launch's own error; with RAFEAST_DEBUG_SYNC=1 in
+// the environment also synchronises and reports execution errors here
+void check_launch(const char* file, int line);
 
 // ---- device control block of one batched COCG solve -------------------------
 struct CocgCtl {
@@ -88,6 +91,7 @@ template <typename T> struct CocgArgs {
   int* colact;           // [m0]: 1 while any shift of column i is active
   CocgCtl* ctl;
   int* hist;             // [max_inner + 2]: active columns after step k, or null
+  double* rhist;         // [max_inner + 2]: max ||r||/||b|| over active systems
   int nc_real;           // shifts with a right-hand side (<= NC)
   double tol2;           // solve_tol^2
   int max_inner;
@@ -131,6 +135,8 @@ struct Handle {
   int opt_profile = 0;
   // kernel time / algorithmic bytes of the COCG kernels (profile option)
   double prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::vector<int> last_hist;        // last profiled filter: active columns per step
+  std::vector<double> last_rhist;    // and the worst relative residual per step
   // scratch, grown on demand and kept
   std::vector<DevBuf> bufs;
   // launch accounting of the current call

@@ -231,6 +231,7 @@ __device__ void cocg_scalar_step(const CocgArgs<T>& a, int NC) {
   __syncthreads();
   const int k = __ldcg(&a.ctl->iter);
   const int nsys = a.m0 * NC;
+  double worst = 0.0;  // max ||r||^2/||b||^2 over systems active at step k
   for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
     SysState st = a.st[s];
     double* acc = a.acc + 5 * s;
@@ -242,6 +243,7 @@ __device__ void cocg_scalar_step(const CocgArgs<T>& a, int NC) {
     bool freeze = !st.active;
     if (st.active) {
       if (k == 0) st.bnorm2 = nu;
+      if (st.bnorm2 > 0.0) worst = fmax(worst, nu / st.bnorm2);
       const bool conv = nu <= a.tol2 * st.bnorm2;
       if (conv || k >= a.max_inner) {
         st.active = 0;
@@ -308,7 +310,22 @@ __device__ void cocg_scalar_step(const CocgArgs<T>& a, int NC) {
     if (any) atomicAdd(&s_cols, 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0 && a.hist && k <= a.max_inner) a.hist[k] = s_cols;
+  if (a.hist) {
+    __shared__ double s_worst[32];
+    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, 16));
+    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, 8));
+    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, 4));
+    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, 2));
+    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, 1));
+    if ((threadIdx.x & 31) == 0) s_worst[threadIdx.x >> 5] = worst;
+    __syncthreads();
+    if (threadIdx.x == 0 && k <= a.max_inner) {
+      double w = 0.0;
+      for (int t = 0; t < (int)(blockDim.x >> 5); ++t) w = fmax(w, s_worst[t]);
+      a.hist[k] = s_cols;
+      a.rhist[k] = sqrt(w);
+    }
+  }
   if (threadIdx.x == 0) {
     CocgCtl* c = a.ctl;
     c->active = s_active;
@@ -576,14 +593,12 @@ __global__ void __launch_bounds__(THREADS) k_spmm_real(int64_t n, const int32_t*
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static int g_num_sms_cache = 0;
 
 template <typename K>
 static int grid_x(K kernel, size_t smem, int num_sms, int64_t rows_needed_groups) {
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, THREADS, smem) != cudaSuccess ||
-      occ < 1)
-    occ = 1;
+  RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, THREADS, smem));
+  if (occ < 1) occ = 1;
   int64_t g = (int64_t)num_sms * occ;
   if (g > rows_needed_groups) g = rows_needed_groups;
   if (g < 1) g = 1;

@@ -52,7 +52,7 @@ EXPORTS = [
     "rafeast_spmm", "rafeast_shifted_spmm", "rafeast_filter", "rafeast_orthonormalize",
     "rafeast_rayleigh_ritz", "rafeast_warmstart", "rafeast_set_subspace",
     "rafeast_get_subspace", "rafeast_solve", "rafeast_solve_batched", "rafeast_profile",
-    "rafeast_last_error",
+    "rafeast_last_error", "rafeast_profile_history",
 ]
 
 
@@ -103,6 +103,7 @@ def load():
         "rafeast_last_error": (C.c_char_p, []),
         "rafeast_set_option": (I, [P, I, I64]),
         "rafeast_profile": (I, [P, I, P]),
+        "rafeast_profile_history": (I, [P, I, P, P]),
         "rafeast_matrix_info": (I, [P, C.POINTER(I64), C.POINTER(I), C.POINTER(D),
                                     C.POINTER(D), C.POINTER(D)]),
         "rafeast_quadrature": (I, [D, D, I, D, P, P]),
@@ -218,6 +219,18 @@ def rafeast_profile(h, reset=True):
     _check(load().rafeast_profile(h, int(reset), _ptr(out)), "rafeast_profile")
     return dict(dots_launches=out[0], dots_ms=out[1], dots_bytes=out[2],
                 update_launches=out[3], update_ms=out[4], update_bytes=out[5])
+
+
+def rafeast_profile_history(h):
+    """(active columns, worst relative residual) per COCG step of the last
+    profiled solve."""
+    lib = load()
+    n = lib.rafeast_profile_history(h, 0, None, None)
+    _check(min(n, 0), "rafeast_profile_history")
+    cols = np.zeros(n, dtype=np.int32)
+    res = np.zeros(n)
+    lib.rafeast_profile_history(h, n, _ptr(cols), _ptr(res))
+    return cols, res
 
 
 def rafeast_matrix_info(h):
