@@ -22,6 +22,7 @@ namespace rafeast {
 static thread_local char g_err[512] = "";
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
+  if (g_err[0]) return;  // keep the first failure of this call
   snprintf(g_err, sizeof(g_err), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
 }
 
@@ -68,6 +69,7 @@ struct CallScope {
     h->launches = 0;
     h->spmm_launches = 0;
     cudaGetLastError();  // a stale error of an earlier call is not ours
+    g_err[0] = 0;
     RF_CUDA(cudaSetDevice(h->device));
     RF_CUDA(cudaEventRecord(h->ev_in, h->user_stream));
     RF_CUDA(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
@@ -307,12 +309,14 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   g_capturing = true;
   try {
     for (int it = 0; it < chunk; ++it) {
-      if (prof) RF_CUDA(cudaEventRecord(evs[2 * it], h->stream));
+      // external records: the graph itself records the event on each replay
+      if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * it], h->stream, cudaEventRecordExternal));
       launch_cocg_dots<T>(a, NC, it & 1, h->num_sms, h->stream);
-      if (prof) RF_CUDA(cudaEventRecord(evs[2 * it + 1], h->stream));
+      if (prof)
+        RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], h->stream, cudaEventRecordExternal));
       launch_cocg_update<T>(a, NC, it & 1, h->num_sms, h->stream);
     }
-    if (prof) RF_CUDA(cudaEventRecord(evs[2 * chunk], h->stream));
+    if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * chunk], h->stream, cudaEventRecordExternal));
   } catch (...) {
     g_capturing = false;
     cudaStreamEndCapture(h->stream, &graph);
@@ -901,6 +905,8 @@ int rafeast_filter(rafeast_t hh, const rafeast_params* prm, const double* Q, con
   try {
     run_filter(h, *prm, Qi, AQi, th_d, th, m0, ldq, Qti, fs);
   } catch (const Err& e) {
+    // a breakdown still returns the filtered block; anything else is fatal
+    if (e.code != RAFEAST_ERR_COCG_BREAKDOWN) throw;
     rc = e.code;
   }
   RF_CUDA(cudaEventRecord(e1, h->stream));

@@ -69,78 +69,91 @@ void choose_shape(int m0, int NC, bool fp64, int forced_lanes, int& lanes, int& 
 }
 
 // ---------------------------------------------------------------------------
-// gather core: acc[c][j] += sum_k val_k * X[col_k][chunk c], chunk active mask
+// gather core. The G lanes of a group own one row: they load up to G CSR
+// entries of the row at once (coalesced) and broadcast them with width-G
+// shuffles, so the gathered loads of consecutive entries do not wait on each
+// other's index loads; two entries are in flight per step.
+// acc[c][j] += sum_k val_k * X[col_k][chunk c] for the lane's active chunks.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned group_mask(int G) {
+  if (G == 32) return 0xffffffffu;
+  const int grp = (threadIdx.x & 31) / G;
+  return ((1u << G) - 1u) << (grp * G);
+}
+
 template <typename T, int NC, int MAXCPL>
 __device__ __forceinline__ void gather_row(const int32_t* __restrict__ colidx,
-                                           const T* __restrict__ val, int k0, int k1,
+                                           const T* __restrict__ val, int k0, int k1, int row,
+                                           int lg, int G, unsigned gmask,
                                            const T* __restrict__ X, int64_t ldx_t,
                                            const int (&coff)[MAXCPL], unsigned mask,
                                            c2<T> (&acc)[MAXCPL][NC]) {
   using C = c2<T>;
-  int k = k0;
-  for (; k + 1 < k1; k += 2) {
-    const int ca = __ldg(colidx + k), cb = __ldg(colidx + k + 1);
-    const T va = __ldg(val + k), vb = __ldg(val + k + 1);
-    C xa[MAXCPL][NC], xb[MAXCPL][NC];
+  for (int kb = k0; kb < k1; kb += G) {
+    const int kk = kb + lg;
+    const int my_c = kk < k1 ? __ldg(colidx + kk) : row;
+    const T my_v = kk < k1 ? __ldg(val + kk) : (T)0;
+    const int cnt = min(G, k1 - kb);
+    for (int e = 0; e < cnt; e += 2) {
+      const int ca = __shfl_sync(gmask, my_c, e, G);
+      const T va = __shfl_sync(gmask, my_v, e, G);
+      const int cb = __shfl_sync(gmask, my_c, e + 1 < cnt ? e + 1 : e, G);
+      const T vb = e + 1 < cnt ? __shfl_sync(gmask, my_v, e + 1, G) : (T)0;
+      C xa[MAXCPL][NC], xb[MAXCPL][NC];
 #pragma unroll
-    for (int c = 0; c < MAXCPL; ++c)
-      if (mask & (1u << c)) {
-        ld_chunk<NC>(X + (int64_t)ca * ldx_t + coff[c], xa[c]);
-        ld_chunk<NC>(X + (int64_t)cb * ldx_t + coff[c], xb[c]);
-      }
-#pragma unroll
-    for (int c = 0; c < MAXCPL; ++c)
-      if (mask & (1u << c)) {
-#pragma unroll
-        for (int j = 0; j < NC; ++j) {
-          acc[c][j] = crfma<T>(va, xa[c][j], acc[c][j]);
-          acc[c][j] = crfma<T>(vb, xb[c][j], acc[c][j]);
+      for (int c = 0; c < MAXCPL; ++c)
+        if (mask & (1u << c)) {
+          ld_chunk<NC>(X + (int64_t)ca * ldx_t + coff[c], xa[c]);
+          ld_chunk<NC>(X + (int64_t)cb * ldx_t + coff[c], xb[c]);
         }
-      }
-  }
-  if (k < k1) {
-    const int ca = __ldg(colidx + k);
-    const T va = __ldg(val + k);
 #pragma unroll
-    for (int c = 0; c < MAXCPL; ++c)
-      if (mask & (1u << c)) {
-        C xa[NC];
-        ld_chunk<NC>(X + (int64_t)ca * ldx_t + coff[c], xa);
+      for (int c = 0; c < MAXCPL; ++c)
+        if (mask & (1u << c)) {
 #pragma unroll
-        for (int j = 0; j < NC; ++j) acc[c][j] = crfma<T>(va, xa[j], acc[c][j]);
-      }
+          for (int j = 0; j < NC; ++j) {
+            acc[c][j] = crfma<T>(va, xa[c][j], acc[c][j]);
+            acc[c][j] = crfma<T>(vb, xb[c][j], acc[c][j]);
+          }
+        }
+    }
   }
 }
 
 // two arrays at once (update kernel): acc_r from R, acc_p from P
 template <typename T, int NC, int MAXCPL>
 __device__ __forceinline__ void gather_row2(const int32_t* __restrict__ colidx,
-                                            const T* __restrict__ val, int k0, int k1,
+                                            const T* __restrict__ val, int k0, int k1, int row,
+                                            int lg, int G, unsigned gmask,
                                             const T* __restrict__ R, const T* __restrict__ P,
                                             int64_t ldx_t, const int (&coff)[MAXCPL],
                                             unsigned mask, c2<T> (&ar)[MAXCPL][NC],
                                             c2<T> (&ap)[MAXCPL][NC]) {
   using C = c2<T>;
-  for (int k = k0; k < k1; ++k) {
-    const int ca = __ldg(colidx + k);
-    const T va = __ldg(val + k);
-    C xr[MAXCPL][NC], xp[MAXCPL][NC];
+  for (int kb = k0; kb < k1; kb += G) {
+    const int kk = kb + lg;
+    const int my_c = kk < k1 ? __ldg(colidx + kk) : row;
+    const T my_v = kk < k1 ? __ldg(val + kk) : (T)0;
+    const int cnt = min(G, k1 - kb);
+    for (int e = 0; e < cnt; ++e) {
+      const int ca = __shfl_sync(gmask, my_c, e, G);
+      const T va = __shfl_sync(gmask, my_v, e, G);
+      C xr[MAXCPL][NC], xp[MAXCPL][NC];
 #pragma unroll
-    for (int c = 0; c < MAXCPL; ++c)
-      if (mask & (1u << c)) {
-        ld_chunk<NC>(R + (int64_t)ca * ldx_t + coff[c], xr[c]);
-        ld_chunk<NC>(P + (int64_t)ca * ldx_t + coff[c], xp[c]);
-      }
-#pragma unroll
-    for (int c = 0; c < MAXCPL; ++c)
-      if (mask & (1u << c)) {
-#pragma unroll
-        for (int j = 0; j < NC; ++j) {
-          ar[c][j] = crfma<T>(va, xr[c][j], ar[c][j]);
-          ap[c][j] = crfma<T>(va, xp[c][j], ap[c][j]);
+      for (int c = 0; c < MAXCPL; ++c)
+        if (mask & (1u << c)) {
+          ld_chunk<NC>(R + (int64_t)ca * ldx_t + coff[c], xr[c]);
+          ld_chunk<NC>(P + (int64_t)ca * ldx_t + coff[c], xp[c]);
         }
-      }
+#pragma unroll
+      for (int c = 0; c < MAXCPL; ++c)
+        if (mask & (1u << c)) {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) {
+            ar[c][j] = crfma<T>(va, xr[c][j], ar[c][j]);
+            ap[c][j] = crfma<T>(va, xp[c][j], ap[c][j]);
+          }
+        }
+    }
   }
 }
 
@@ -344,10 +357,11 @@ __device__ void cocg_scalar_step(const CocgArgs<T>& a, int NC) {
 // COCG dots kernel
 // ---------------------------------------------------------------------------
 template <typename T, int NC, int MAXCPL>
-__global__ void __launch_bounds__(THREADS) k_cocg_dots(CocgArgs<T> a, int buf) {
+__global__ void __launch_bounds__(THREADS, 1) k_cocg_dots(CocgArgs<T> a, int buf) {
   using C = c2<T>;
   if (__ldcg(&a.ctl->done)) return;
   const RowMap mp = row_map(a.lanes, a.cpl);
+  const unsigned gmask = group_mask(mp.G);
   const int ibase = blockIdx.y * mp.G * mp.cpl + mp.lg;
   const T* __restrict__ R = a.r[buf];
   const int64_t ldt = (int64_t)a.ldc * 2;
@@ -378,7 +392,8 @@ __global__ void __launch_bounds__(THREADS) k_cocg_dots(CocgArgs<T> a, int buf) {
       for (int c = 0; c < MAXCPL; ++c)
 #pragma unroll
         for (int j = 0; j < NC; ++j) acc[c][j] = mk<T>((T)0, (T)0);
-      gather_row<T, NC, MAXCPL>(a.colidx, a.val, k0, k1, R, ldt, coff, mask, acc);
+      gather_row<T, NC, MAXCPL>(a.colidx, a.val, k0, k1, (int)row, mp.lg, mp.G, gmask, R, ldt,
+                                coff, mask, acc);
 #pragma unroll
       for (int c = 0; c < MAXCPL; ++c)
         if (mask & (1u << c)) {
@@ -448,10 +463,11 @@ __global__ void __launch_bounds__(THREADS) k_cocg_dots(CocgArgs<T> a, int buf) {
 // COCG update kernel
 // ---------------------------------------------------------------------------
 template <typename T, int NC, int MAXCPL>
-__global__ void __launch_bounds__(THREADS) k_cocg_update(CocgArgs<T> a, int buf) {
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_cocg_update(CocgArgs<T> a, int buf) {
   using C = c2<T>;
   if (__ldcg(&a.ctl->done)) return;
   const RowMap mp = row_map(a.lanes, a.cpl);
+  const unsigned gmask = group_mask(mp.G);
   const int ibase = blockIdx.y * mp.G * mp.cpl + mp.lg;
   const T* __restrict__ R = a.r[buf];
   const T* __restrict__ P = a.p[buf];
@@ -485,7 +501,8 @@ __global__ void __launch_bounds__(THREADS) k_cocg_update(CocgArgs<T> a, int buf)
     for (int c = 0; c < MAXCPL; ++c)
 #pragma unroll
       for (int j = 0; j < NC; ++j) ar[c][j] = ap[c][j] = mk<T>((T)0, (T)0);
-    gather_row2<T, NC, MAXCPL>(a.colidx, a.val, k0, k1, R, P, ldt, coff, mask, ar, ap);
+    gather_row2<T, NC, MAXCPL>(a.colidx, a.val, k0, k1, (int)row, mp.lg, mp.G, gmask, R, P, ldt,
+                               coff, mask, ar, ap);
 #pragma unroll
     for (int c = 0; c < MAXCPL; ++c)
       if (mask & (1u << c)) {
@@ -523,6 +540,7 @@ __global__ void __launch_bounds__(THREADS) k_shifted_spmm(int64_t n, const int32
                                                           const T* P, T* W, int G, int cpl) {
   using C = c2<T>;
   const RowMap mp = row_map(G, cpl);
+  const unsigned gmask = group_mask(G);
   const int ibase = blockIdx.y * G * cpl + mp.lg;
   const int64_t ldt = (int64_t)ldc * 2;
   const C* zs = reinterpret_cast<const C*>(zsp);
@@ -544,7 +562,8 @@ __global__ void __launch_bounds__(THREADS) k_shifted_spmm(int64_t n, const int32
     for (int c = 0; c < MAXCPL; ++c)
 #pragma unroll
       for (int j = 0; j < NC; ++j) acc[c][j] = mk<T>((T)0, (T)0);
-    gather_row<T, NC, MAXCPL>(ci, val, __ldg(rp + row), __ldg(rp + row + 1), P, ldt, coff, mask, acc);
+    gather_row<T, NC, MAXCPL>(ci, val, __ldg(rp + row), __ldg(rp + row + 1), (int)row, mp.lg, G,
+                              gmask, P, ldt, coff, mask, acc);
 #pragma unroll
     for (int c = 0; c < MAXCPL; ++c)
       if (mask & (1u << c)) {
@@ -564,6 +583,7 @@ __global__ void __launch_bounds__(THREADS) k_spmm_real(int64_t n, const int32_t*
                                                        int G, int cpl) {
   using C = c2<T>;
   const RowMap mp = row_map(G, cpl);
+  const unsigned gmask = group_mask(G);
   const int ibase = blockIdx.y * G * cpl + mp.lg;
   int coff[MAXCPL];
   unsigned mask = 0;
@@ -578,7 +598,8 @@ __global__ void __launch_bounds__(THREADS) k_spmm_real(int64_t n, const int32_t*
     C acc[MAXCPL][1];
 #pragma unroll
     for (int c = 0; c < MAXCPL; ++c) acc[c][0] = mk<T>((T)0, (T)0);
-    gather_row<T, 1, MAXCPL>(ci, val, __ldg(rp + row), __ldg(rp + row + 1), X, ld, coff, mask, acc);
+    gather_row<T, 1, MAXCPL>(ci, val, __ldg(rp + row), __ldg(rp + row + 1), (int)row, mp.lg, G,
+                             gmask, X, ld, coff, mask, acc);
 #pragma unroll
     for (int c = 0; c < MAXCPL; ++c)
       if (mask & (1u << c)) {
