@@ -384,7 +384,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_cocg_dots(CocgArgs<T> a, int buf
 #pragma unroll
     for (int j = 0; j < NC; ++j) dg_re[c][j] = dg_im[c][j] = dd_re[c][j] = dd_im[c][j] = dn[c][j] = (T)0;
 
-  if (mask) {
+  // every lane of a group must run the row loop (its shuffles name the whole
+  // group); lanes without a chunk take part but load nothing
+  if (__any_sync(0xffffffffu, mask != 0)) {
     for (int64_t row = mp.gid; row < a.n; row += mp.gstride) {
       const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
       C acc[MAXCPL][NC];
@@ -493,7 +495,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_cocg_update
     coff[c] = i * NC * 2;
     if (c < mp.cpl && i < a.m0 && __ldcg(a.colact + i)) mask |= 1u << c;
   }
-  if (!mask) return;
+  // warp-uniform exit: the gathers shuffle across the whole lane group
+  if (!__any_sync(0xffffffffu, mask != 0)) return;
   for (int64_t row = mp.gid; row < a.n; row += mp.gstride) {
     const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
     C ar[MAXCPL][NC], ap[MAXCPL][NC];
@@ -555,7 +558,8 @@ __global__ void __launch_bounds__(THREADS) k_shifted_spmm(int64_t n, const int32
     coff[c] = i * NC * 2;
     if (c < cpl && i < m) mask |= 1u << c;
   }
-  if (!mask) return;
+  // warp-uniform exit: the gathers shuffle across the whole lane group
+  if (!__any_sync(0xffffffffu, mask != 0)) return;
   for (int64_t row = mp.gid; row < n; row += mp.gstride) {
     C acc[MAXCPL][NC];
 #pragma unroll
@@ -593,7 +597,8 @@ __global__ void __launch_bounds__(THREADS) k_spmm_real(int64_t n, const int32_t*
     coff[c] = i * 2;
     if (c < cpl && i < mc) mask |= 1u << c;
   }
-  if (!mask) return;
+  // warp-uniform exit: the gathers shuffle across the whole lane group
+  if (!__any_sync(0xffffffffu, mask != 0)) return;
   for (int64_t row = mp.gid; row < n; row += mp.gstride) {
     C acc[MAXCPL][1];
 #pragma unroll
