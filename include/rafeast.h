@@ -162,11 +162,14 @@ int rafeast_set_option(rafeast_t h, int key, int64_t value);
 int rafeast_profile(rafeast_t h, int reset, double* out);
 
 /* Per-step history of the last COCG solve run with RAFEAST_OPT_PROFILE on:
- * for step k, the number of subspace columns with a still-active shift and
- * the largest ||r_k||_2/||b||_2 over the active systems. Copies at most
- * max_len entries into the host arrays (either may be NULL) and returns the
- * history length (0 when nothing was profiled), or -1 for a NULL handle. */
-int rafeast_profile_history(rafeast_t h, int max_len, int* active_cols, double* max_relres);
+ * for step k, the number of subspace columns with a still-active shift, the
+ * largest ||r_k||_2/||b||_2 over the active systems, and the milliseconds of
+ * the step's dot kernel and update kernel (kernel_ms[2k], kernel_ms[2k+1]).
+ * Copies at most max_len steps into the host arrays (any may be NULL) and
+ * returns the history length (0 when nothing was profiled), or -1 for a NULL
+ * handle. */
+int rafeast_profile_history(rafeast_t h, int max_len, int* active_cols, double* max_relres,
+                            double* kernel_ms);
 
 /* Matrix facts: n, internal reorder flag (1 when rows are permuted), ||A||_1
  * and the Gershgorin interval of A. Any output pointer may be NULL. */

@@ -354,6 +354,7 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
     std::vector<int> hist(iters + 1, 0);
     RF_CUDA(cudaMemcpy(hist.data(), a.hist, sizeof(int) * iters, cudaMemcpyDeviceToHost));
     h->last_hist.assign(hist.begin(), hist.begin() + iters);
+    h->last_tk.assign(tk.begin(), tk.begin() + std::min<size_t>(tk.size(), 2 * (size_t)iters));
     h->last_rhist.assign(iters, 0.0);
     RF_CUDA(cudaMemcpy(h->last_rhist.data(), a.rhist, sizeof(double) * iters,
                        cudaMemcpyDeviceToHost));
@@ -714,13 +715,18 @@ int rafeast_profile(rafeast_t hh, int reset, double* out) {
   return RAFEAST_OK;
 }
 
-int rafeast_profile_history(rafeast_t hh, int max_len, int* active_cols, double* max_relres) {
+int rafeast_profile_history(rafeast_t hh, int max_len, int* active_cols, double* max_relres,
+                            double* kernel_ms) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || max_len < 0) return RAFEAST_ERR_INVALID_ARG;
   const int len = (int)h->last_hist.size();
   for (int k = 0; k < std::min(len, max_len); ++k) {
     if (active_cols) active_cols[k] = h->last_hist[k];
     if (max_relres) max_relres[k] = h->last_rhist[k];
+    if (kernel_ms) {
+      kernel_ms[2 * k] = 2 * k < (int)h->last_tk.size() ? h->last_tk[2 * k] : 0.0;
+      kernel_ms[2 * k + 1] = 2 * k + 1 < (int)h->last_tk.size() ? h->last_tk[2 * k + 1] : 0.0;
+    }
   }
   return len;
 }

@@ -137,6 +137,7 @@ struct Handle {
   double prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   std::vector<int> last_hist;        // last profiled filter: active columns per step
   std::vector<double> last_rhist;    // and the worst relative residual per step
+  std::vector<float> last_tk;        // dot, update kernel milliseconds per step
   // scratch, grown on demand and kept
   std::vector<DevBuf> bufs;
   // launch accounting of the current call

@@ -103,7 +103,7 @@ def load():
         "rafeast_last_error": (C.c_char_p, []),
         "rafeast_set_option": (I, [P, I, I64]),
         "rafeast_profile": (I, [P, I, P]),
-        "rafeast_profile_history": (I, [P, I, P, P]),
+        "rafeast_profile_history": (I, [P, I, P, P, P]),
         "rafeast_matrix_info": (I, [P, C.POINTER(I64), C.POINTER(I), C.POINTER(D),
                                     C.POINTER(D), C.POINTER(D)]),
         "rafeast_quadrature": (I, [D, D, I, D, P, P]),
@@ -222,15 +222,16 @@ def rafeast_profile(h, reset=True):
 
 
 def rafeast_profile_history(h):
-    """(active columns, worst relative residual) per COCG step of the last
-    profiled solve."""
+    """(active columns, worst relative residual, [dot ms, update ms]) per
+    COCG step of the last profiled solve."""
     lib = load()
-    n = lib.rafeast_profile_history(h, 0, None, None)
+    n = lib.rafeast_profile_history(h, 0, None, None, None)
     _check(min(n, 0), "rafeast_profile_history")
     cols = np.zeros(n, dtype=np.int32)
     res = np.zeros(n)
-    lib.rafeast_profile_history(h, n, _ptr(cols), _ptr(res))
-    return cols, res
+    ms = np.zeros((n, 2))
+    lib.rafeast_profile_history(h, n, _ptr(cols), _ptr(res), _ptr(ms))
+    return cols, res, ms
 
 
 def rafeast_matrix_info(h):
