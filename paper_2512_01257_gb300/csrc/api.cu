@@ -230,9 +230,13 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
     zs[j].x = (T)(zr[jj] - h->shift);
     zs[j].y = (T)zi[jj];
   }
+  // kernel family: bulk-copy gathers for float32 with NC >= 2 (default),
+  // register gathers otherwise
+  const bool use_tma = !fp64 && NC >= 2 && h->opt_kernel != 1;
   // device buffers
   const int ldc = even(m0 * NC);
-  const size_t state_elems = (size_t)h->n * ldc * 2;
+  size_t state_elems = (size_t)h->n * ldc * 2;
+  if (use_tma) state_elems = (size_t)h->n * m0 * NC * 2;  // blocked, no padding
   T* state = (T*)scratch(h, S_STATE, 4 * state_elems * sizeof(T));
   const int ldd = m0;
   T* dacc = (T*)scratch(h, S_DACC, (size_t)h->n * ldd * sizeof(T));
@@ -291,7 +295,19 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   a.tol2 = prm.solve_tol * prm.solve_tol;
   a.max_inner = prm.max_inner;
   a.form = prm.solve_form;
-  launch_cocg_init<T>(a, NC, h->num_sms, h->stream);
+  a.wait_cycles = h->opt_wait_cycles;
+  a.stall_bytes = h->opt_stall_bytes;
+  const int maxnz = h->opt_maxnz;
+  if constexpr (sizeof(T) == 4) {
+    if (use_tma) {
+      launch_cocg_reset<T>(a, NC, h->stream);
+      launch_cocg_tma(a, NC, 0, 0, maxnz, h->num_sms, h->stream);
+    } else {
+      launch_cocg_init<T>(a, NC, h->num_sms, h->stream);
+    }
+  } else {
+    launch_cocg_init<T>(a, NC, h->num_sms, h->stream);
+  }
   h->launches += 2;
   // capture `chunk` COCG steps as one graph (with event nodes around every
   // kernel when profiling, so kernel times are measured inside the replays)
@@ -311,10 +327,20 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
     for (int it = 0; it < chunk; ++it) {
       // external records: the graph itself records the event on each replay
       if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * it], h->stream, cudaEventRecordExternal));
-      launch_cocg_dots<T>(a, NC, it & 1, h->num_sms, h->stream);
+      if constexpr (sizeof(T) == 4) {
+        if (use_tma) launch_cocg_tma(a, NC, 1, it & 1, maxnz, h->num_sms, h->stream);
+        else launch_cocg_dots<T>(a, NC, it & 1, h->num_sms, h->stream);
+      } else {
+        launch_cocg_dots<T>(a, NC, it & 1, h->num_sms, h->stream);
+      }
       if (prof)
         RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], h->stream, cudaEventRecordExternal));
-      launch_cocg_update<T>(a, NC, it & 1, h->num_sms, h->stream);
+      if constexpr (sizeof(T) == 4) {
+        if (use_tma) launch_cocg_tma(a, NC, 2, it & 1, maxnz, h->num_sms, h->stream);
+        else launch_cocg_update<T>(a, NC, it & 1, h->num_sms, h->stream);
+      } else {
+        launch_cocg_update<T>(a, NC, it & 1, h->num_sms, h->stream);
+      }
     }
     if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * chunk], h->stream, cudaEventRecordExternal));
   } catch (...) {
@@ -374,7 +400,7 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
       }
     }
   }
-  if (!ctl.done) throw Err{RAFEAST_ERR_TIMEOUT};
+  if (!ctl.done || ctl.timeout) throw Err{RAFEAST_ERR_TIMEOUT};
   fs.iters_max = ctl.max_iters;
   fs.iters_min = ctl.min_iters;
   fs.breakdown = ctl.breakdown;
@@ -691,6 +717,22 @@ int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
       return RAFEAST_OK;
     case RAFEAST_OPT_AUTOTUNE:
       h->opt_autotune = value ? 1 : 0;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_KERNEL:
+      if (value < 0 || value > 2) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_kernel = (int)value;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_MAXNZ:
+      if (value < 1 || value > 32) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_maxnz = (int)value;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_WAIT_LIMIT:
+      if (value < 1) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_wait_cycles = (long long)value;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_TEST_STALL:
+      if (value < 0 || value > 4096 || (value % 16) != 0) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_stall_bytes = (int)value;
       return RAFEAST_OK;
     case RAFEAST_OPT_PROFILE:
       h->opt_profile = value ? 1 : 0;

@@ -47,6 +47,7 @@ struct CocgCtl {
   int capped;           // systems stopped by max_inner
   int max_iters;        // most iterations taken by any system
   int min_iters;        // fewest iterations taken by a system with b != 0
+  int timeout;          // a bounded device wait ran out
 };
 
 // per-system scalar state, double precision (one struct per system s)
@@ -96,6 +97,8 @@ template <typename T> struct CocgArgs {
   double tol2;           // solve_tol^2
   int max_inner;
   int form;              // RAFEAST_FORM_*
+  long long wait_cycles; // bound of one bulk-copy wait (clock64 cycles)
+  int stall_bytes;       // test hook: extra bytes each stage expects (0)
 };
 
 // ---- handle -----------------------------------------------------------------
@@ -133,6 +136,10 @@ struct Handle {
   int opt_autotune = 1;
   int opt_lanes = 0;
   int opt_profile = 0;
+  int opt_kernel = 0;  // 0 auto, 1 register gathers, 2 bulk-copy gathers
+  int opt_maxnz = 8;   // nonzeros per bulk-copy item
+  long long opt_wait_cycles = 2000000000LL;  // ~1 s: bound of one device wait
+  int opt_stall_bytes = 0;                   // test hook, see RAFEAST_OPT_TEST_STALL
   // kernel time / algorithmic bytes of the COCG kernels (profile option)
   double prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   std::vector<int> last_hist;        // last profiled filter: active columns per step
@@ -170,6 +177,14 @@ void choose_shape(int m0, int NC, bool fp64, int forced_lanes, int& lanes, int& 
 
 template <typename T>
 void launch_cocg_init(const CocgArgs<T>& a, int NC, int num_sms, cudaStream_t s);
+template <typename T>
+void launch_cocg_reset(const CocgArgs<T>& a, int NC, cudaStream_t s);
+// bulk-copy (TMA) kernels, float32, NC in {2, 4, 8}, blocked state layout
+// (kernels_tma.cu). which: 0 init, 1 dots, 2 update.
+void launch_cocg_tma(const CocgArgs<float>& a, int NC, int which, int buf, int maxnz,
+                     int num_sms, cudaStream_t s);
+int tma_cpl(int m0);
+int tma_ncb(int m0, int cpl);
 template <typename T>
 void launch_cocg_dots(const CocgArgs<T>& a, int NC, int buf, int num_sms, cudaStream_t s);
 template <typename T>

@@ -45,6 +45,10 @@ RAFEAST_OPT_CHUNK = 2
 RAFEAST_OPT_AUTOTUNE = 3
 RAFEAST_OPT_LANES = 4
 RAFEAST_OPT_PROFILE = 5
+RAFEAST_OPT_KERNEL = 6
+RAFEAST_OPT_MAXNZ = 7
+RAFEAST_OPT_WAIT_LIMIT = 8
+RAFEAST_OPT_TEST_STALL = 9
 
 EXPORTS = [
     "rafeast_create", "rafeast_destroy", "rafeast_status_string", "rafeast_set_option",

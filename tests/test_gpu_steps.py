@@ -216,3 +216,66 @@ def test_filter_mixed(lib, form, nc):
         assert np.linalg.norm(got - exp) <= 1e-3 * np.linalg.norm(exp)
     finally:
         lib.rafeast_destroy(h)
+
+
+# ---- bulk-copy (TMA) gathers vs register gathers ---------------------------------
+
+@pytest.mark.parametrize("m0,nc", [(5, 2), (33, 4), (40, 3), (80, 4), (96, 8), (70, 2)])
+def test_bulk_copy_and_register_kernels_agree(lib, m0, nc):
+    """Same COCG steps through both gather kernels and through the oracle:
+    empty rows (no diagonal entry), a dense row spanning many copy items,
+    block widths that are not multiples of 32."""
+    import torch
+    n = 1531
+    rp, ci, va, a = rand_sym_csr(n, 7)
+    shift = 0.5
+    h = lib.rafeast_create(rp, ci, va, shift)
+    try:
+        q0 = OF.random_start(n, m0, 1)
+        Q = colmajor_dev(q0)
+        outs = []
+        for kern in (1, 2):
+            lib.rafeast_set_option(h, lib.RAFEAST_OPT_KERNEL, kern)
+            Qt = torch.zeros_like(Q)
+            prm = lib.make_params(1.0, 1.6, m0, nc, 1.0, 0.0, 1e-10, 1, 12, lib.RAFEAST_MIXED,
+                                  lib.RAFEAST_FORM_CORRECTION)
+            info = lib.rafeast_filter(h, prm, Q, None, Qt)
+            assert info.cocg_max_last == 12
+            outs.append(from_colmajor(Qt))
+        A = (a + shift * sp.identity(n)).tocsr()
+        z, w = OQ.nodes(1.0, 1.6, nc, 1.0)
+        exp, _ = OF.filter_apply(A, q0, z, w, 0.0, 12, "correction")
+        scale = np.linalg.norm(exp)
+        assert np.linalg.norm(outs[0] - outs[1]) <= 2e-5 * scale
+        assert np.linalg.norm(outs[1] - exp) <= 2e-5 * scale
+    finally:
+        lib.rafeast_destroy(h)
+
+
+def test_bounded_wait_expiry_is_reported_and_context_survives(lib):
+    """A stage that expects bytes no copy delivers: the bounded wait runs out,
+    the solve stops with RAFEAST_ERR_TIMEOUT, and the next call works."""
+    import torch
+    lap, lmin, lmax = _filter_case()
+    m0 = 11
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    try:
+        q0 = OF.random_start(lap.n, m0, 3)
+        Q = colmajor_dev(q0)
+        Qt = torch.zeros_like(Q)
+        prm = lib.make_params(lmin, lmax, m0, 4, 1.0, 1e-5, 1e-10, 1, 200, lib.RAFEAST_MIXED,
+                              lib.RAFEAST_FORM_CORRECTION)
+        lib.rafeast_set_option(h, lib.RAFEAST_OPT_WAIT_LIMIT, 2_000_000)
+        lib.rafeast_set_option(h, lib.RAFEAST_OPT_TEST_STALL, 16)
+        with pytest.raises(lib.RafeastError) as err:
+            lib.rafeast_filter(h, prm, Q, None, Qt)
+        assert err.value.code == lib.RAFEAST_ERR_TIMEOUT
+        lib.rafeast_set_option(h, lib.RAFEAST_OPT_TEST_STALL, 0)
+        lib.rafeast_set_option(h, lib.RAFEAST_OPT_WAIT_LIMIT, 2_000_000_000)
+        lib.rafeast_filter(h, prm, Q, None, Qt)
+        z, w = OQ.nodes(lmin, lmax, 4, 1.0)
+        exp, _ = OF.filter_apply(lap.scipy(), q0, z, w, 1e-13, 4000, "correction")
+        assert np.linalg.norm(from_colmajor(Qt) - exp) <= 1e-3 * np.linalg.norm(exp)
+        assert torch.cuda.synchronize() is None
+    finally:
+        lib.rafeast_destroy(h)
