@@ -81,9 +81,9 @@ extern "C" {
 #define RAFEAST_OPT_AUTOTUNE 3      /* 1 (default) time SpMM shapes, 0 off     */
 #define RAFEAST_OPT_LANES 4         /* force lanes per row (4,8,16,32), 0 auto */
 #define RAFEAST_OPT_PROFILE 5       /* 1: time every COCG kernel in the graph  */
-#define RAFEAST_OPT_KERNEL 6        /* COCG kernels: 0 auto (bulk-copy gathers *
-                                     * for float32 with N_c >= 2), 1 register *
-                                     * gathers, 2 bulk-copy gathers            */
+#define RAFEAST_OPT_KERNEL 6        /* COCG kernels: 0 auto (register gathers),*
+                                     * 1 register gathers, 2 bulk-copy (TMA)   *
+                                     * gathers (float32, N_c >= 2)             */
 #define RAFEAST_OPT_MAXNZ 7         /* nonzeros per bulk-copy item (1..32)     */
 #define RAFEAST_OPT_WAIT_LIMIT 8    /* clock cycles one device-side wait may   *
                                      * spin before the solve stops with        *

@@ -232,7 +232,7 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   }
   // kernel family: bulk-copy gathers for float32 with NC >= 2 (default),
   // register gathers otherwise
-  const bool use_tma = !fp64 && NC >= 2 && h->opt_kernel != 1;
+  const bool use_tma = !fp64 && NC >= 2 && h->opt_kernel == 2;
   // device buffers
   const int ldc = even(m0 * NC);
   size_t state_elems = (size_t)h->n * ldc * 2;
