@@ -6,10 +6,11 @@ outer_tol) of the workload below, inputs resident in HBM. Prints one JSON line.
 
 Default workload (``knn200k``): kNN graph Laplacian of 200,000 uniform points
 in [0,1]^3 (seed 2), k = 10, union-symmetrised, unit weights, + 1e-3 I; the
-64 smallest eigenvalues; m0 = 80, N_c = 4, p = 20, q = 2, COCG tolerance
-1e-4, outer tolerance 1e-11, relaxed inner solves (COCG tolerance 1e-2, at most
-100 steps), mixed precision (float32 shifted solves, double outer loop). The inputs (COCG state 4 x n x 640 x 4 B = 2.05 GB) are larger
-than L2, so no flush is needed between steps.
+64 smallest eigenvalues; m0 = 80, N_c = 4, p = 20, q = 2, outer tolerance
+1e-11, relaxed inner solves (COCG tolerance 1e-2, at most 100 steps), mixed
+precision (float32 shifted solves, double outer loop). The inputs (COCG state
+4 x n x 640 x 4 B = 2.05 GB) are larger than L2, so no flush is needed
+between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
