@@ -242,6 +242,13 @@ int rafeast_filter(rafeast_t h, const rafeast_params* prm, const double* Q,
  * block is rank deficient beyond what a shift repairs. */
 int rafeast_orthonormalize(rafeast_t h, int m, double* Q, double* R);
 
+/* Gram matrix G = X^T Y of two tall blocks (the Cholesky-QR Gram matrix
+ * B_Q = Q~^T Q~ and the Rayleigh-Ritz matrix A_Q = Q^T (A Q) of Algorithm 1
+ * are of this form). X, Y: device, n x m column-major (n of the handle);
+ * G: device, m x m column-major, entry (a, b) = sum_i X(i, a) Y(i, b), FP64.
+ * Per-CTA partial sums live in the handle's scratch. m in 1..128. */
+int rafeast_gram(rafeast_t h, int m, const double* X, const double* Y, double* G);
+
 /* Rayleigh-Ritz (Algorithm 1): A_Q = Q^T A Q = V L V^T with L ascending,
  * Q <- Q V in place; theta (host, m) receives L and resid (host, m, may be
  * NULL) the relative residuals ||A q_i - l_i q_i||_2 / ||A||_1. Q must have

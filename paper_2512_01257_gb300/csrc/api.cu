@@ -21,6 +21,10 @@ namespace rafeast {
 
 static thread_local char g_err[512] = "";
 
+void set_last_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+void clear_last_error() { g_err[0] = 0; }
+
 void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
   if (g_err[0]) return;  // keep the first failure of this call
   snprintf(g_err, sizeof(g_err), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
@@ -1001,6 +1005,26 @@ int rafeast_orthonormalize(rafeast_t hh, int m, double* Q, double* R) {
       for (int j = 0; j < m; ++j) R[(size_t)j * m + i] = Rt[(size_t)i * m + j];
   }
   scope.finish();
+  return RAFEAST_OK;
+  API_END
+}
+
+int rafeast_gram(rafeast_t hh, int m, const double* X, const double* Y, double* G) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || m < 1 || m > 128 || !X || !Y || !G) return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  CallScope scope(h);
+  const int ld = even(m);
+  double* Xi = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ld);
+  double* Yi = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ld);
+  launch_to_internal(h->n, m, X, Xi, ld, h->perm, h->stream);
+  launch_to_internal(h->n, m, Y, Yi, ld, h->perm, h->stream);
+  DenseWs d = dense_ws(h, m);
+  // row-major (Y^T X)[b][a] = sum_r Y[r][b] X[r][a] is G = X^T Y in column-major order
+  gram(Yi, Xi, h->n, m, ld, G, d.part, h->num_sms, h->stream);
+  h->launches += 4;
+  scope.finish();
+  RF_CUDA(cudaStreamSynchronize(h->stream));
   return RAFEAST_OK;
   API_END
 }

@@ -33,6 +33,8 @@ struct Err {
   } while (0)
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line);
+void set_last_message(const char* msg);  // replaces the text of rafeast_last_error
+void clear_last_error();
 // after a kernel launch: the launch's own error; with RAFEAST_DEBUG_SYNC=1 in
 // the environment also synchronises and reports execution errors here
 void check_launch(const char* file, int line);

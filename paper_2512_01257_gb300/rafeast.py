@@ -56,7 +56,7 @@ EXPORTS = [
     "rafeast_spmm", "rafeast_shifted_spmm", "rafeast_filter", "rafeast_orthonormalize",
     "rafeast_rayleigh_ritz", "rafeast_warmstart", "rafeast_set_subspace",
     "rafeast_get_subspace", "rafeast_solve", "rafeast_solve_batched", "rafeast_profile",
-    "rafeast_last_error", "rafeast_profile_history",
+    "rafeast_last_error", "rafeast_profile_history", "rafeast_gram",
 ]
 
 
@@ -118,6 +118,7 @@ def load():
         "rafeast_filter": (I, [P, C.POINTER(RafeastParams), P, P, P, C.POINTER(RafeastInfo)]),
         "rafeast_orthonormalize": (I, [P, I, P, P]),
         "rafeast_rayleigh_ritz": (I, [P, I, P, P, P]),
+        "rafeast_gram": (I, [P, I, P, P, P]),
         "rafeast_warmstart": (I, [P, D, D, I, I, I, U64]),
         "rafeast_set_subspace": (I, [P, P, I, I]),
         "rafeast_get_subspace": (I, [P, P, P, I, I]),
@@ -293,6 +294,12 @@ def rafeast_orthonormalize(h, m, Q, want_r=False):
     R = np.zeros((m, m)) if want_r else None
     _check(load().rafeast_orthonormalize(h, m, _ptr(Q), _ptr(R)), "rafeast_orthonormalize")
     return None if R is None else R.T.copy()  # column-major -> (row, col)
+
+
+def rafeast_gram(h, m, X, Y, G):
+    """G = X^T Y; X, Y CUDA tensors (m, n) (column-major n x m), G CUDA (m, m)
+    holding the column-major m x m result (G[b, a] = entry (a, b))."""
+    return _check(load().rafeast_gram(h, m, _ptr(X), _ptr(Y), _ptr(G)), "rafeast_gram")
 
 
 def rafeast_rayleigh_ritz(h, m, Q):

