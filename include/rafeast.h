@@ -249,6 +249,27 @@ int rafeast_orthonormalize(rafeast_t h, int m, double* Q, double* R);
  * Per-CTA partial sums live in the handle's scratch. m in 1..128. */
 int rafeast_gram(rafeast_t h, int m, const double* X, const double* Y, double* G);
 
+/* Allocation-free Gram matrix (no counterpart in the paper; a service for
+ * callers): the same G = X^T Y as rafeast_gram, without a handle and without
+ * any device allocation during the call. Some callers cannot let a library
+ * allocate: applications that reserve the whole device memory up front for
+ * their own allocator, or code that must not stall on cudaMalloc/cudaFree
+ * (both can synchronise the device). Here the per-CTA partial sums live in a
+ * fixed 2 MiB device array compiled into the library, held by every GPU that
+ * loads it until the process exits.
+ *   X, Y: device, n x m column-major (leading dimension n); G: device, m x m
+ *   column-major, entry (a, b) = sum_i X(i, a) Y(i, b); n >= 1, 1 <= m <= 64
+ *   (larger m returns -1 and rafeast_last_error says why). stream: a
+ *   cudaStream_t on the current device; the call only enqueues work, G is
+ *   ready when the stream reaches it.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) and caches it; make that first call before any
+ *   stream capture begins. All calls share the array: calls whose work
+ *   overlaps on the GPU (other streams, other threads) race on it and must be
+ *   serialised by the caller. */
+int rafeast_gram_noalloc(const double* X, const double* Y, int64_t n, int m, double* G,
+                         void* stream);
+
 /* Rayleigh-Ritz (Algorithm 1): A_Q = Q^T A Q = V L V^T with L ascending,
  * Q <- Q V in place; theta (host, m) receives L and resid (host, m, may be
  * NULL) the relative residuals ||A q_i - l_i q_i||_2 / ||A||_1. Q must have

@@ -19,7 +19,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librafeast.so")
-SOURCES = ["kernels_sparse.cu", "kernels_tma.cu", "kernels_dense.cu", "api.cu", "hostmath.cpp"]
+SOURCES = ["kernels_sparse.cu", "kernels_tma.cu", "kernels_dense.cu", "api.cu", "noalloc.cu",
+           "hostmath.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -57,6 +57,7 @@ EXPORTS = [
     "rafeast_rayleigh_ritz", "rafeast_warmstart", "rafeast_set_subspace",
     "rafeast_get_subspace", "rafeast_solve", "rafeast_solve_batched", "rafeast_profile",
     "rafeast_last_error", "rafeast_profile_history", "rafeast_gram",
+    "rafeast_gram_noalloc",
 ]
 
 
@@ -119,6 +120,7 @@ def load():
         "rafeast_orthonormalize": (I, [P, I, P, P]),
         "rafeast_rayleigh_ritz": (I, [P, I, P, P, P]),
         "rafeast_gram": (I, [P, I, P, P, P]),
+        "rafeast_gram_noalloc": (I, [P, P, I64, I, P, P]),
         "rafeast_warmstart": (I, [P, D, D, I, I, I, U64]),
         "rafeast_set_subspace": (I, [P, P, I, I]),
         "rafeast_get_subspace": (I, [P, P, P, I, I]),
@@ -300,6 +302,13 @@ def rafeast_gram(h, m, X, Y, G):
     """G = X^T Y; X, Y CUDA tensors (m, n) (column-major n x m), G CUDA (m, m)
     holding the column-major m x m result (G[b, a] = entry (a, b))."""
     return _check(load().rafeast_gram(h, m, _ptr(X), _ptr(Y), _ptr(G)), "rafeast_gram")
+
+
+def rafeast_gram_noalloc(X, Y, n, m, G, stream=None):
+    """Allocation-free G = X^T Y (same layouts as rafeast_gram, no handle).
+    Enqueues on ``stream`` (default: torch's current stream) and returns."""
+    return _check(load().rafeast_gram_noalloc(_ptr(X), _ptr(Y), n, m, _ptr(G), _stream(stream)),
+                  "rafeast_gram_noalloc")
 
 
 def rafeast_rayleigh_ritz(h, m, Q):
