@@ -88,6 +88,10 @@ extern "C" {
 #define RAFEAST_OPT_WAIT_LIMIT 8    /* clock cycles one device-side wait may   *
                                      * spin before the solve stops with        *
                                      * RAFEAST_ERR_TIMEOUT (default 2e9, ~1 s) */
+#define RAFEAST_OPT_CPL 10          /* cap on subspace columns per lane in the *
+                                     * register-gather kernels (0: automatic); *
+                                     * a lower cap means narrower column       *
+                                     * blocks, fewer registers, more warps     */
 #define RAFEAST_OPT_TEST_STALL 9    /* test hook: bytes (multiple of 16) that  *
                                      * every bulk-copy stage waits for and no *
                                      * copy delivers, so the bounded wait     *

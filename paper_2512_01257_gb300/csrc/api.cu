@@ -275,7 +275,7 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   a.m0 = m0;
   a.ldc = ldc;
   int colblocks = 1;
-  choose_shape(m0, NC, fp64, h->opt_lanes, a.lanes, a.cpl, colblocks);
+  choose_shape(m0, NC, fp64, h->opt_lanes, a.lanes, a.cpl, colblocks, h->opt_cpl);
   a.r[0] = state;
   a.r[1] = state + state_elems;
   a.p[0] = state + 2 * state_elems;
@@ -738,6 +738,10 @@ int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
       if (value < 0 || value > 4096 || (value % 16) != 0) return RAFEAST_ERR_INVALID_ARG;
       h->opt_stall_bytes = (int)value;
       return RAFEAST_OK;
+    case RAFEAST_OPT_CPL:
+      if (value < 0 || value > 16) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_cpl = (int)value;
+      return RAFEAST_OK;
     case RAFEAST_OPT_PROFILE:
       h->opt_profile = value ? 1 : 0;
       return RAFEAST_OK;
@@ -873,7 +877,7 @@ int rafeast_shifted_spmm(rafeast_t hh, int nc, const double* z, int m, const dou
     hz[2 * j + 1] = z[2 * jj + 1];
   }
   int lanes, cpl, cb;
-  choose_shape(m, NC, fp64, h->opt_lanes, lanes, cpl, cb);
+  choose_shape(m, NC, fp64, h->opt_lanes, lanes, cpl, cb, h->opt_cpl);
   std::vector<double> hout(hin.size());
   if (fp64) {
     double* zs = (double*)scratch(h, S_SMALL, sizeof(double) * 2 * NC + 64);

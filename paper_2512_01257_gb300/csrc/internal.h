@@ -137,6 +137,7 @@ struct Handle {
   int opt_chunk = 16;
   int opt_autotune = 1;
   int opt_lanes = 0;
+  int opt_cpl = 0;     // cap on column chunks per lane (0: kernel maximum)
   int opt_profile = 0;
   int opt_kernel = 0;  // 0 auto, 1 register gathers, 2 bulk-copy gathers
   int opt_maxnz = 8;   // nonzeros per bulk-copy item
@@ -175,7 +176,7 @@ int64_t bandwidth(int64_t n, const int32_t* rowptr, const int32_t* colidx,
 int nc_pad(int nc);  // shifts rounded up to a compiled NC (1, 2, 4, 8)
 int max_cpl(int NC, bool fp64);
 void choose_shape(int m0, int NC, bool fp64, int forced_lanes, int& lanes, int& cpl,
-                  int& colblocks);
+                  int& colblocks, int forced_cpl);
 
 template <typename T>
 void launch_cocg_init(const CocgArgs<T>& a, int NC, int num_sms, cudaStream_t s);

@@ -38,6 +38,12 @@ template <typename T> constexpr int maxcpl_of(int NC);
 template <> constexpr int maxcpl_of<float>(int NC) { return NC >= 12 ? 1 : 12 / NC; }
 template <> constexpr int maxcpl_of<double>(int NC) { return NC >= 8 ? 1 : 8 / NC; }
 
+// a narrower instantiation (fewer chunks per lane, fewer registers, more
+// resident warps) used when the chosen shape needs no more chunks than it has
+template <typename T> constexpr int small_cpl_of(int NC);
+template <> constexpr int small_cpl_of<float>(int NC) { return NC >= 4 ? 1 : 4 / NC; }
+template <> constexpr int small_cpl_of<double>(int NC) { return NC >= 8 ? 1 : 8 / NC; }
+
 int nc_pad(int nc) {
   if (nc <= 1) return 1;
   if (nc <= 2) return 2;
@@ -47,8 +53,9 @@ int nc_pad(int nc) {
 int max_cpl(int NC, bool fp64) { return fp64 ? maxcpl_of<double>(NC) : maxcpl_of<float>(NC); }
 
 void choose_shape(int m0, int NC, bool fp64, int forced_lanes, int& lanes, int& cpl,
-                  int& colblocks) {
-  const int mc = max_cpl(NC, fp64);
+                  int& colblocks, int forced_cpl) {
+  int mc = max_cpl(NC, fp64);
+  if (forced_cpl > 0 && forced_cpl < mc) mc = forced_cpl;
   double best = -1.0;
   const int cands[4] = {32, 16, 8, 4};
   for (int t = 0; t < 4; ++t) {
@@ -235,7 +242,8 @@ __global__ void __launch_bounds__(THREADS) k_cocg_init(CocgArgs<T> a) {
 // COCG dots kernel
 // ---------------------------------------------------------------------------
 template <typename T, int NC, int MAXCPL>
-__global__ void __launch_bounds__(THREADS, 1) k_cocg_dots(CocgArgs<T> a, int buf) {
+__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && MAXCPL * NC <= 4) ? 2 : 1)
+    k_cocg_dots(CocgArgs<T> a, int buf) {
   using C = c2<T>;
   if (__ldcg(&a.ctl->done)) return;
   const RowMap mp = row_map(a.lanes, a.cpl);
@@ -343,7 +351,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_cocg_dots(CocgArgs<T> a, int buf
 // COCG update kernel
 // ---------------------------------------------------------------------------
 template <typename T, int NC, int MAXCPL>
-__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_cocg_update(CocgArgs<T> a, int buf) {
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1)
+    k_cocg_update(CocgArgs<T> a, int buf) {
   using C = c2<T>;
   if (__ldcg(&a.ctl->done)) return;
   const RowMap mp = row_map(a.lanes, a.cpl);
@@ -509,9 +518,8 @@ static int grid_x(K kernel, size_t smem, int num_sms, int64_t rows_needed_groups
   return (int)g;
 }
 
-template <typename T, int NC>
-static void dispatch_dots(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
-  constexpr int MC = maxcpl_of<T>(NC);
+template <typename T, int NC, int MC>
+static void dispatch_dots_mc(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
   auto kern = k_cocg_dots<T, NC, MC>;
   const size_t smem = (size_t)a.lanes * MC * NC * 5 * sizeof(double);
   const int colblocks = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);
@@ -521,9 +529,8 @@ static void dispatch_dots(const CocgArgs<T>& a, int buf, int num_sms, cudaStream
   RF_LAUNCH();
 }
 
-template <typename T, int NC>
-static void dispatch_update(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
-  constexpr int MC = maxcpl_of<T>(NC);
+template <typename T, int NC, int MC>
+static void dispatch_update_mc(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
   auto kern = k_cocg_update<T, NC, MC>;
   const size_t smem = (size_t)a.lanes * MC * NC * sizeof(Coef<T>);
   const int colblocks = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);
@@ -537,6 +544,20 @@ template <typename T>
 void launch_cocg_reset(const CocgArgs<T>& a, int NC, cudaStream_t s) {
   k_cocg_reset<T><<<(a.m0 * NC + 255) / 256, 256, 0, s>>>(a, NC);
   RF_LAUNCH();
+}
+
+template <typename T, int NC>
+static void dispatch_dots(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
+  constexpr int SC = small_cpl_of<T>(NC), MC = maxcpl_of<T>(NC);
+  if (SC < MC && a.cpl <= SC) dispatch_dots_mc<T, NC, SC>(a, buf, num_sms, s);
+  else dispatch_dots_mc<T, NC, MC>(a, buf, num_sms, s);
+}
+
+template <typename T, int NC>
+static void dispatch_update(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
+  constexpr int SC = small_cpl_of<T>(NC), MC = maxcpl_of<T>(NC);
+  if (SC < MC && a.cpl <= SC) dispatch_update_mc<T, NC, SC>(a, buf, num_sms, s);
+  else dispatch_update_mc<T, NC, MC>(a, buf, num_sms, s);
 }
 
 template <typename T>
@@ -612,7 +633,7 @@ void launch_spmm_real(int64_t n, const int32_t* rp, const int32_t* ci, const T* 
   constexpr int MC = maxcpl_of<T>(1);
   const int mc = (k + 1) / 2;
   int G, cpl, blocks;
-  choose_shape(mc, 1, sizeof(T) == 8, 0, G, cpl, blocks);
+  choose_shape(mc, 1, sizeof(T) == 8, 0, G, cpl, blocks, 0);
   auto kern = k_spmm_real<T, MC>;
   const int64_t groups = (n + (int64_t)WARPS * (32 / G) - 1) / ((int64_t)WARPS * (32 / G));
   dim3 grid(grid_x(kern, 0, num_sms, groups), blocks);

@@ -49,6 +49,7 @@ RAFEAST_OPT_KERNEL = 6
 RAFEAST_OPT_MAXNZ = 7
 RAFEAST_OPT_WAIT_LIMIT = 8
 RAFEAST_OPT_TEST_STALL = 9
+RAFEAST_OPT_CPL = 10
 
 EXPORTS = [
     "rafeast_create", "rafeast_destroy", "rafeast_status_string", "rafeast_set_option",
