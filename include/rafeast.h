@@ -92,6 +92,11 @@ extern "C" {
                                      * register-gather kernels (0: automatic); *
                                      * a lower cap means narrower column       *
                                      * blocks, fewer registers, more warps     */
+#define RAFEAST_OPT_SOLVER 11       /* shifted solves: 0 one COCG per shift,   *
+                                     * 1 multi-shift COCG (one seed recurrence *
+                                     * per column, other shifts from its       *
+                                     * scalars; same iterates in exact         *
+                                     * arithmetic)                              */
 #define RAFEAST_OPT_TEST_STALL 9    /* test hook: bytes (multiple of 16) that  *
                                      * every bulk-copy stage waits for and no *
                                      * copy delivers, so the bounded wait     *

@@ -268,6 +268,7 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   RF_CUDA(cudaMemcpyAsync(sc + o_fin, finit.data(), sizeof(double) * m0, cudaMemcpyHostToDevice,
                           h->stream));
   CocgArgs<T> a;
+  memset(&a, 0, sizeof(a));
   a.n = h->n;
   a.rowptr = h->rowptr;
   a.colidx = h->colidx;
@@ -415,6 +416,226 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
   if (fs.breakdown) throw Err{RAFEAST_ERR_COCG_BREAKDOWN};
 }
 
+// multi-shift COCG filter: one seed Krylov recurrence per column (the shift
+// nearest the real axis), every other shift from the seed's scalars; same
+// Q~ as filter_dev in exact arithmetic, a quarter of the gathered bytes at
+// N_c = 4.
+template <typename T>
+static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd,
+                          const double* AQd, const double* theta_d,
+                          const std::vector<double>& theta, int m0, int ldq, double* Qt,
+                          FilterStats& fs) {
+  using C = c2<T>;
+  const int nc = prm.nc;
+  const bool fp64 = sizeof(T) == 8;
+  std::vector<double> zr, zi, wr, wi;
+  quadrature_nodes(prm.lmin, prm.lmax, nc, prm.ellipse_ratio, zr, zi, wr, wi);
+  int seed = 0;
+  for (int j = 1; j < nc; ++j)
+    if (zi[j] < zi[seed]) seed = j;
+  const int ns = nc - 1;
+  std::vector<int> others;
+  for (int j = 0; j < nc; ++j)
+    if (j != seed) others.push_back(j);
+  const bool corr = prm.solve_form == RAFEAST_FORM_CORRECTION;
+  const int pairs = (m0 + 1) / 2, ncol = 2 * pairs;
+  auto coef_of = [&](int j, int i) {
+    if (i >= m0) return make_double2(0.0, 0.0);
+    if (!corr) return make_double2(wr[j], wi[j]);
+    const double dr = zr[j] - theta[i], di = zi[j];
+    const double den = dr * dr + di * di;
+    return make_double2((wr[j] * dr + wi[j] * di) / den, (wi[j] * dr - wr[j] * di) / den);
+  };
+  std::vector<double2> coef(ncol), scoef((size_t)ncol * std::max(ns, 1));
+  std::vector<double> finit(m0, 0.0);
+  for (int i = 0; i < ncol; ++i) {
+    coef[i] = coef_of(seed, i);
+    for (int t = 0; t < ns; ++t) scoef[(size_t)i * ns + t] = coef_of(others[t], i);
+  }
+  if (corr)
+    for (int i = 0; i < m0; ++i)
+      for (int j = 0; j < nc; ++j) finit[i] += coef_of(j, i).x;
+  std::vector<double2> sigma(std::max(ns, 1));
+  for (int t = 0; t < ns; ++t)
+    sigma[t] = make_double2(zr[others[t]] - zr[seed], zi[others[t]] - zi[seed]);
+  std::vector<C> zs(2);
+  zs[0].x = zs[1].x = (T)(zr[seed] - h->shift);
+  zs[0].y = zs[1].y = (T)zi[seed];
+  // device buffers
+  const int ldc = ncol;                     // seed arrays: complex per row
+  const int ldps = pairs * ns * 2;          // shifted directions: complex per row
+  const size_t seed_elems = (size_t)h->n * ldc * 2;
+  const size_t ps_elems = (size_t)h->n * std::max(ldps, 1) * 2;
+  T* state = (T*)scratch(h, S_STATE, (4 * seed_elems + ps_elems) * sizeof(T));
+  const int ldd = ncol;
+  T* dacc = (T*)scratch(h, S_DACC, (size_t)h->n * ldd * sizeof(T));
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    size_t o = off;
+    off += bytes;
+    return o;
+  };
+  const size_t o_acc = carve(sizeof(double) * 5 * ncol);
+  const size_t o_st = carve(sizeof(SysState) * ncol);
+  const size_t o_cf = carve(sizeof(Coef<T>) * ncol);
+  const size_t o_col = carve(sizeof(int) * pairs);
+  const size_t o_ctl = carve(sizeof(CocgCtl));
+  const size_t o_zs = carve(sizeof(C) * 2);
+  const size_t o_coef = carve(sizeof(double2) * ncol);
+  const size_t o_fin = carve(sizeof(double) * m0);
+  const size_t o_sig = carve(sizeof(double2) * sigma.size());
+  const size_t o_scoef = carve(sizeof(double2) * scoef.size());
+  const size_t o_sst = carve(sizeof(ShiftState) * scoef.size());
+  const size_t o_scf = carve(sizeof(ShiftCoef<T>) * scoef.size());
+  const size_t o_hist = carve(sizeof(int) * ((size_t)prm.max_inner + 2));
+  const size_t o_rhist = carve(sizeof(double) * ((size_t)prm.max_inner + 2));
+  char* sc = (char*)scratch(h, S_SCAL, off + 256);
+  RF_CUDA(cudaMemcpyAsync(sc + o_zs, zs.data(), sizeof(C) * 2, cudaMemcpyHostToDevice, h->stream));
+  RF_CUDA(cudaMemcpyAsync(sc + o_coef, coef.data(), sizeof(double2) * ncol, cudaMemcpyHostToDevice,
+                          h->stream));
+  RF_CUDA(cudaMemcpyAsync(sc + o_fin, finit.data(), sizeof(double) * m0, cudaMemcpyHostToDevice,
+                          h->stream));
+  RF_CUDA(cudaMemcpyAsync(sc + o_sig, sigma.data(), sizeof(double2) * sigma.size(),
+                          cudaMemcpyHostToDevice, h->stream));
+  RF_CUDA(cudaMemcpyAsync(sc + o_scoef, scoef.data(), sizeof(double2) * scoef.size(),
+                          cudaMemcpyHostToDevice, h->stream));
+  CocgArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.n = h->n;
+  a.rowptr = h->rowptr;
+  a.colidx = h->colidx;
+  a.val = fp64 ? (const T*)h->val64 : (const T*)h->val32;
+  a.m0 = pairs;
+  a.ldc = ldc;
+  int colblocks = 1;
+  choose_shape(pairs, 2, fp64, h->opt_lanes, a.lanes, a.cpl, colblocks,
+               h->opt_cpl > 0 ? std::min(h->opt_cpl, ms_max_cpl(fp64)) : ms_max_cpl(fp64));
+  a.r[0] = state;
+  a.r[1] = state + seed_elems;
+  a.p[0] = state + 2 * seed_elems;
+  a.p[1] = state + 3 * seed_elems;
+  a.ps = state + 4 * seed_elems;
+  a.ldps = ldps;
+  a.dacc = dacc;
+  a.ldd = ldd;
+  a.qin = Qd;
+  a.aqin = AQd;
+  a.ldq = ldq;
+  a.theta = theta_d;
+  a.zs = sc + o_zs;
+  a.coef = (const double2*)(sc + o_coef);
+  a.acc = (double*)(sc + o_acc);
+  a.st = (SysState*)(sc + o_st);
+  a.cf = (Coef<T>*)(sc + o_cf);
+  a.colact = (int*)(sc + o_col);
+  a.ctl = (CocgCtl*)(sc + o_ctl);
+  a.hist = h->opt_profile ? (int*)(sc + o_hist) : nullptr;
+  a.rhist = h->opt_profile ? (double*)(sc + o_rhist) : nullptr;
+  a.nc_real = 2;
+  a.tol2 = prm.solve_tol * prm.solve_tol;
+  a.max_inner = prm.max_inner;
+  a.form = prm.solve_form;
+  a.wait_cycles = h->opt_wait_cycles;
+  a.ms = 1;
+  a.ns = ns;
+  a.nc_total = nc;
+  a.sigma = (const double2*)(sc + o_sig);
+  a.scoef = (const double2*)(sc + o_scoef);
+  a.sst = (ShiftState*)(sc + o_sst);
+  a.scf = (ShiftCoef<T>*)(sc + o_scf);
+  launch_ms_init<T>(a, m0, h->num_sms, h->stream);
+  h->launches += 2;
+  int chunk = std::max(2, h->opt_chunk);
+  chunk += chunk & 1;
+  const bool prof = h->opt_profile != 0;
+  std::vector<cudaEvent_t> evs;
+  if (prof) {
+    evs.resize(2 * chunk + 1);
+    for (auto& e : evs) RF_CUDA(cudaEventCreate(&e));
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  RF_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  g_capturing = true;
+  try {
+    for (int it = 0; it < chunk; ++it) {
+      if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * it], h->stream, cudaEventRecordExternal));
+      launch_cocg_dots<T>(a, 2, it & 1, h->num_sms, h->stream);
+      if (prof)
+        RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], h->stream, cudaEventRecordExternal));
+      launch_ms_update<T>(a, it & 1, h->num_sms, h->stream);
+    }
+    if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * chunk], h->stream, cudaEventRecordExternal));
+  } catch (...) {
+    g_capturing = false;
+    cudaStreamEndCapture(h->stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto& e : evs) cudaEventDestroy(e);
+    throw;
+  }
+  g_capturing = false;
+  RF_CUDA(cudaStreamEndCapture(h->stream, &graph));
+  RF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  CocgCtl ctl;
+  const int max_replays = (prm.max_inner + 2) / chunk + 2;
+  int replays = 0;
+  std::vector<float> tk;
+  for (; replays < max_replays; ++replays) {
+    RF_CUDA(cudaGraphLaunch(exec, h->stream));
+    RF_CUDA(cudaMemcpyAsync(&ctl, a.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    if (prof)
+      for (int it = 0; it < 2 * chunk; ++it) {
+        float ms = 0.f;
+        RF_CUDA(cudaEventElapsedTime(&ms, evs[it], evs[it + 1]));
+        tk.push_back(ms);
+      }
+    if (ctl.done) break;
+  }
+  h->launches += 2 * chunk * (replays + 1);
+  h->spmm_launches += 2 * chunk * (replays + 1);
+  RF_CUDA(cudaGraphExecDestroy(exec));
+  RF_CUDA(cudaGraphDestroy(graph));
+  for (auto& e : evs) RF_CUDA(cudaEventDestroy(e));
+  if (prof && ctl.done) {
+    const int iters = std::min(ctl.iter, prm.max_inner + 1);
+    std::vector<int> hist(iters + 1, 0);
+    RF_CUDA(cudaMemcpy(hist.data(), a.hist, sizeof(int) * iters, cudaMemcpyDeviceToHost));
+    h->last_hist.assign(hist.begin(), hist.begin() + iters);
+    h->last_rhist.assign(iters, 0.0);
+    RF_CUDA(cudaMemcpy(h->last_rhist.data(), a.rhist, sizeof(double) * iters,
+                       cudaMemcpyDeviceToHost));
+    h->last_tk.assign(tk.begin(), tk.begin() + std::min<size_t>(tk.size(), 2 * (size_t)iters));
+    // algorithmic bytes: A once; seed pair-columns (r read by the dot kernel;
+    // r, p read and written by the update kernel); shifted directions read and
+    // written; quadrature sum read and written. hist counts active pairs.
+    const double sv = fp64 ? 8.0 : 4.0;
+    const double abytes = (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
+    const double pairb = (double)h->n * 2 * 2.0 * sv;  // one pair of one complex array
+    for (int k = 0; k < iters && 2 * k + 1 < (int)tk.size(); ++k) {
+      const int act_d = k == 0 ? pairs : hist[k - 1];
+      const int act_u = hist[k];
+      h->prof[0] += 1;
+      h->prof[1] += tk[2 * k];
+      h->prof[2] += abytes + pairb * act_d;
+      if (act_u > 0) {
+        h->prof[3] += 1;
+        h->prof[4] += tk[2 * k + 1];
+        h->prof[5] += abytes + (4.0 + 2.0 * ns) * pairb * act_u + 2.0 * (double)h->n * 2 * act_u * sv;
+      }
+    }
+  }
+  if (!ctl.done || ctl.timeout) throw Err{RAFEAST_ERR_TIMEOUT};
+  fs.iters_max = ctl.max_iters;
+  fs.iters_min = ctl.min_iters;
+  fs.breakdown = ctl.breakdown;
+  fs.capped = ctl.capped;
+  launch_combine<T>(Qd, ldq, dacc, ldd, (const double*)(sc + o_fin), h->n, m0, Qt, h->stream);
+  h->launches += 1;
+  if (fs.breakdown) throw Err{RAFEAST_ERR_COCG_BREAKDOWN};
+}
+
 static void validate_params(const rafeast_params* p) {
   RF_CHECK(p, RAFEAST_ERR_INVALID_ARG);
   RF_CHECK(std::isfinite(p->lmin) && std::isfinite(p->lmax) && p->lmin < p->lmax,
@@ -434,10 +655,14 @@ static void validate_params(const rafeast_params* p) {
 static void run_filter(Handle* h, const rafeast_params& prm, const double* Qd, const double* AQd,
                        const double* theta_d, const std::vector<double>& theta, int m0, int ldq,
                        double* Qt, FilterStats& fs) {
-  if (prm.precision == RAFEAST_FP64)
-    filter_dev<double>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, Qt, fs);
-  else
-    filter_dev<float>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, Qt, fs);
+  const bool ms = h->opt_solver == 1 && h->opt_kernel != 2;
+  if (prm.precision == RAFEAST_FP64) {
+    if (ms) filter_ms_dev<double>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, Qt, fs);
+    else filter_dev<double>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, Qt, fs);
+  } else {
+    if (ms) filter_ms_dev<float>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, Qt, fs);
+    else filter_dev<float>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, Qt, fs);
+  }
 }
 
 // column-major caller block (host or device) -> internal row-major device
@@ -737,6 +962,10 @@ int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
     case RAFEAST_OPT_TEST_STALL:
       if (value < 0 || value > 4096 || (value % 16) != 0) return RAFEAST_ERR_INVALID_ARG;
       h->opt_stall_bytes = (int)value;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_SOLVER:
+      if (value < 0 || value > 1) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_solver = (int)value;
       return RAFEAST_OK;
     case RAFEAST_OPT_CPL:
       if (value < 0 || value > 16) return RAFEAST_ERR_INVALID_ARG;

@@ -68,6 +68,20 @@ template <typename T> struct Coef {
   T pad;
 };
 
+// multi-shift COCG: per (column i, non-seed shift j') scalar state and the
+// coefficients the update kernel consumes
+struct ShiftState {
+  double2 zeta;       // zeta_k of the shifted system (residual = zeta_k r_k)
+  double2 zeta_prev;  // zeta_{k-1}
+  int active;
+  int iters;
+};
+template <typename T> struct ShiftCoef {
+  typename std::conditional<sizeof(T) == 4, float2, double2>::type zeta, beta, ca;
+  T act;  // 1 while the shifted system iterates, else 0 (p_j frozen)
+  T pad;
+};
+
 // arguments of the batched COCG kernels (one problem or a concatenation)
 template <typename T> struct CocgArgs {
   int64_t n;
@@ -101,6 +115,18 @@ template <typename T> struct CocgArgs {
   int form;              // RAFEAST_FORM_*
   long long wait_cycles; // bound of one bulk-copy wait (clock64 cycles)
   int stall_bytes;       // test hook: extra bytes each stage expects (0)
+  // multi-shift mode (ms = 1): the dot kernel runs on column pairs of the
+  // seed shift (m0 = pairs, NC = 2, both zs entries z_seed - sigma); systems
+  // are the 2*pairs columns; the shifted systems live in ps/sst/scf
+  int ms;
+  int ns;                  // non-seed shifts
+  int nc_total;            // real shifts (seed included)
+  const double2* sigma;    // [ns]: z_j - z_seed
+  const double2* scoef;    // [columns * ns]: quadrature coefficient c_j(i)
+  ShiftState* sst;         // [columns * ns]
+  ShiftCoef<T>* scf;       // [columns * ns]
+  T* ps;                   // shifted directions, row r: pairs x ns x 2 complex
+  int ldps;                // complex stride of a ps row
 };
 
 // ---- handle -----------------------------------------------------------------
@@ -138,6 +164,7 @@ struct Handle {
   int opt_autotune = 1;
   int opt_lanes = 0;
   int opt_cpl = 0;     // cap on column chunks per lane (0: kernel maximum)
+  int opt_solver = 0;  // 0: COCG per shift, 1: multi-shift COCG
   int opt_profile = 0;
   int opt_kernel = 0;  // 0 auto, 1 register gathers, 2 bulk-copy gathers
   int opt_maxnz = 8;   // nonzeros per bulk-copy item
@@ -182,6 +209,12 @@ template <typename T>
 void launch_cocg_init(const CocgArgs<T>& a, int NC, int num_sms, cudaStream_t s);
 template <typename T>
 void launch_cocg_reset(const CocgArgs<T>& a, int NC, cudaStream_t s);
+// multi-shift COCG (seed dot kernel = launch_cocg_dots with NC = 2)
+template <typename T>
+void launch_ms_init(const CocgArgs<T>& a, int m_real, int num_sms, cudaStream_t s);
+template <typename T>
+void launch_ms_update(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s);
+int ms_max_cpl(bool fp64);
 // bulk-copy (TMA) kernels, float32, NC in {2, 4, 8}, blocked state layout
 // (kernels_tma.cu). which: 0 init, 1 dots, 2 update.
 void launch_cocg_tma(const CocgArgs<float>& a, int NC, int which, int buf, int maxnz,

@@ -76,6 +76,17 @@ void choose_shape(int m0, int NC, bool fp64, int forced_lanes, int& lanes, int& 
   }
 }
 
+template <typename K>
+static int grid_x(K kernel, size_t smem, int num_sms, int64_t rows_needed_groups) {
+  int occ = 0;
+  RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, THREADS, smem));
+  if (occ < 1) occ = 1;
+  int64_t g = (int64_t)num_sms * occ;
+  if (g > rows_needed_groups) g = rows_needed_groups;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
 // ---------------------------------------------------------------------------
 // gather core. The G lanes of a group own one row: they load up to G CSR
 // entries of the row at once (coalesced) and broadcast them with width-G
@@ -343,7 +354,8 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && MAXCPL * NC <= 4) 
   __syncthreads();
   if (s_last) {
     __threadfence();
-    cocg_scalar_step<T>(a, NC);
+    if (a.ms) ms_scalar_step<T>(a);
+    else cocg_scalar_step<T>(a, NC);
   }
 }
 
@@ -419,6 +431,221 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1)
       }
   }
 }
+
+// ---------------------------------------------------------------------------
+// multi-shift COCG: reset, init, update. The seed's R and P use the NC = 2
+// chunk layout over column pairs (pair q = columns 2q, 2q+1, complex offset
+// row*ldc + 2q); the shifted directions ps hold, for pair q and non-seed
+// shift t, columns 2q and 2q+1 at complex offset row*ldps + 2*(q*ns + t).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_ms_reset(CocgArgs<T> a) {
+  const int ncol = 2 * a.m0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncol; i += gridDim.x * blockDim.x) {
+    SysState st;
+    st.gamma_prev = make_double2(1.0, 0.0);
+    st.alpha_prev = make_double2(1.0, 0.0);
+    st.bnorm2 = 0.0;
+    st.active = 1;
+    st.iters = 0;
+    a.st[i] = st;
+    for (int q = 0; q < 5; ++q) a.acc[5 * i + q] = 0.0;
+    if ((i & 1) == 0) a.colact[i / 2] = 1;
+    for (int t = 0; t < a.ns; ++t) {
+      ShiftState ss;
+      ss.zeta = make_double2(1.0, 0.0);
+      ss.zeta_prev = make_double2(1.0, 0.0);
+      ss.active = 1;
+      ss.iters = 0;
+      a.sst[i * a.ns + t] = ss;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    CocgCtl c;
+    c.ticket = 0;
+    c.iter = 0;
+    c.active = ncol;
+    c.done = 0;
+    c.breakdown = 0;
+    c.capped = 0;
+    c.max_iters = 0;
+    c.min_iters = 0;
+    c.timeout = 0;
+    *a.ctl = c;
+  }
+}
+
+// r0 = b for every column (b = 0 in a padding column), p = ps = 0, D = 0;
+// a.qin/aqin hold m_real = ldq-strided columns, a.m0 is the pair count
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_ms_init(CocgArgs<T> a, int m_real) {
+  const int ncol = 2 * a.m0;
+  const int64_t total = a.n * (int64_t)ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = e / ncol;
+    const int i = (int)(e - row * ncol);
+    double b = 0.0;
+    if (i < m_real) {
+      b = a.qin[row * a.ldq + i];
+      if (a.form == RAFEAST_FORM_CORRECTION) b = a.aqin[row * a.ldq + i] - a.theta[i] * b;
+    }
+    const int64_t off = (row * a.ldc + i) * 2;
+    a.r[0][off] = (T)b;
+    a.r[0][off + 1] = (T)0;
+    a.p[0][off] = (T)0;
+    a.p[0][off + 1] = (T)0;
+    a.dacc[row * a.ldd + i] = (T)0;
+    const int q = i >> 1, h = i & 1;
+    for (int t = 0; t < a.ns; ++t) {
+      const int64_t po = (row * a.ldps + 2 * ((int64_t)q * a.ns + t) + h) * 2;
+      a.ps[po] = (T)0;
+      a.ps[po + 1] = (T)0;
+    }
+  }
+}
+
+template <typename T, int NS, int MAXCPL>
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1)
+    k_ms_update(CocgArgs<T> a, int buf) {
+  using C = c2<T>;
+  if (__ldcg(&a.ctl->done)) return;
+  const RowMap mp = row_map(a.lanes, a.cpl);
+  const unsigned gmask = group_mask(mp.G);
+  const int qbase = blockIdx.y * mp.G * mp.cpl + mp.lg;
+  const T* __restrict__ R = a.r[buf];
+  const T* __restrict__ P = a.p[buf];
+  T* __restrict__ Rn = a.r[buf ^ 1];
+  T* __restrict__ Pn = a.p[buf ^ 1];
+  const int64_t ldt = (int64_t)a.ldc * 2;
+  const C zsd = reinterpret_cast<const C*>(a.zs)[0];
+  // stage the block's coefficients: seed (2 per pair), shifts (2*NS per pair)
+  extern __shared__ unsigned char smem_raw[];
+  Coef<T>* scf = reinterpret_cast<Coef<T>*>(smem_raw);
+  const int q0 = blockIdx.y * mp.G * mp.cpl;
+  const int npair = min(mp.G * mp.cpl, a.m0 - q0);
+  ShiftCoef<T>* ssc = reinterpret_cast<ShiftCoef<T>*>(smem_raw + sizeof(Coef<T>) * 2 * mp.G * mp.cpl);
+  for (int t = threadIdx.x; t < 2 * npair; t += blockDim.x) scf[t] = a.cf[2 * q0 + t];
+  if (NS > 0)
+    for (int t = threadIdx.x; t < 2 * npair * NS; t += blockDim.x) ssc[t] = a.scf[2 * q0 * NS + t];
+  __syncthreads();
+  int coff[MAXCPL];
+  unsigned mask = 0;
+#pragma unroll
+  for (int c = 0; c < MAXCPL; ++c) {
+    const int q = qbase + c * mp.G;
+    coff[c] = q * 2 * 2;
+    if (c < mp.cpl && q < a.m0 && __ldcg(a.colact + q)) mask |= 1u << c;
+  }
+  if (!__any_sync(0xffffffffu, mask != 0)) return;  // warp-uniform
+  for (int64_t row = mp.gid; row < a.n; row += mp.gstride) {
+    const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
+    C ar[MAXCPL][2], ap[MAXCPL][2];
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) ar[c][h] = ap[c][h] = mk<T>((T)0, (T)0);
+    gather_row2<T, 2, MAXCPL>(a.colidx, a.val, k0, k1, (int)row, mp.lg, mp.G, gmask, R, P, ldt,
+                              coff, mask, ar, ap);
+#pragma unroll
+    for (int c = 0; c < MAXCPL; ++c)
+      if (mask & (1u << c)) {
+        const int q = qbase + c * mp.G, ql = q - q0;
+        C rv[2], pv[2], rn[2];
+        ld_chunk<2>(R + row * ldt + coff[c], rv);
+        ld_chunk<2>(P + row * ldt + coff[c], pv);
+        T dsum[2] = {(T)0, (T)0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const Coef<T> cf = scf[2 * ql + h];
+          const C pn = cfma<T>(cf.beta, pv[h], mk<T>(cf.ar * rv[h].x, cf.ar * rv[h].y));
+          const C lpn = cfma<T>(cf.beta, ap[c][h], mk<T>(cf.ar * ar[c][h].x, cf.ar * ar[c][h].y));
+          const C sv = csub<T>(cmul<T>(zsd, pn), lpn);
+          rn[h] = csub<T>(rv[h], cmul<T>(cf.alpha, sv));
+          pv[h] = pn;
+          dsum[h] = fma(cf.ca.x, pn.x, fma(-cf.ca.y, pn.y, dsum[h]));
+        }
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+          const ShiftCoef<T> s0 = ssc[(2 * ql) * NS + t];
+          const ShiftCoef<T> s1 = ssc[(2 * ql + 1) * NS + t];
+          if (s0.act != (T)0 || s1.act != (T)0) {
+            T* pp = a.ps + (row * a.ldps + 2 * ((int64_t)q * NS + t)) * 2;
+            C pj[2];
+            ldcg_chunk<2>(pp, pj);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const ShiftCoef<T>& sc = h ? s1 : s0;
+              if (sc.act != (T)0) {
+                // p_j^k = zeta_k r_k + beta_j p_j^{k-1}; x_j += alpha_j p_j^k
+                pj[h] = cfma<T>(sc.beta, pj[h], cmul<T>(sc.zeta, rv[h]));
+                dsum[h] = fma(sc.ca.x, pj[h].x, fma(-sc.ca.y, pj[h].y, dsum[h]));
+              }
+            }
+            st_chunk<2>(pp, pj);
+          }
+        }
+        st_chunk<2>(Rn + row * ldt + coff[c], rn);
+        st_chunk<2>(Pn + row * ldt + coff[c], pv);
+        T* dp = a.dacc + row * a.ldd + 2 * q;
+        dp[0] += dsum[0];
+        dp[1] += dsum[1];
+      }
+  }
+}
+
+template <typename T, int NS>
+static void dispatch_ms_update(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
+  constexpr int MCS = 2, MCL = sizeof(T) == 4 ? 4 : 2;
+  const size_t smem = (size_t)2 * a.lanes * a.cpl * (sizeof(Coef<T>) + NS * sizeof(ShiftCoef<T>)) + 16;
+  const int colblocks = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);
+  const int64_t groups = (a.n + (int64_t)WARPS * (32 / a.lanes) - 1) / ((int64_t)WARPS * (32 / a.lanes));
+  if (a.cpl <= MCS) {
+    auto kern = k_ms_update<T, NS, MCS>;
+    dim3 grid(grid_x(kern, smem, num_sms, groups), colblocks);
+    kern<<<grid, THREADS, smem, s>>>(a, buf);
+  } else {
+    if (a.cpl > MCL) throw Err{RAFEAST_ERR_INVALID_ARG};
+    auto kern = k_ms_update<T, NS, MCL>;
+    dim3 grid(grid_x(kern, smem, num_sms, groups), colblocks);
+    kern<<<grid, THREADS, smem, s>>>(a, buf);
+  }
+  RF_LAUNCH();
+}
+
+int ms_max_cpl(bool fp64) { return fp64 ? 2 : 4; }
+
+template <typename T>
+void launch_ms_init(const CocgArgs<T>& a, int m_real, int num_sms, cudaStream_t s) {
+  k_ms_reset<T><<<(2 * a.m0 + 255) / 256, 256, 0, s>>>(a);
+  RF_LAUNCH();
+  const int64_t total = a.n * (int64_t)(2 * a.m0);
+  int64_t blocks = (total + THREADS - 1) / THREADS;
+  if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
+  if (blocks < 1) blocks = 1;
+  k_ms_init<T><<<(int)blocks, THREADS, 0, s>>>(a, m_real);
+  RF_LAUNCH();
+}
+
+template <typename T>
+void launch_ms_update(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
+  switch (a.ns) {
+    case 0: dispatch_ms_update<T, 0>(a, buf, num_sms, s); break;
+    case 1: dispatch_ms_update<T, 1>(a, buf, num_sms, s); break;
+    case 2: dispatch_ms_update<T, 2>(a, buf, num_sms, s); break;
+    case 3: dispatch_ms_update<T, 3>(a, buf, num_sms, s); break;
+    case 4: dispatch_ms_update<T, 4>(a, buf, num_sms, s); break;
+    case 5: dispatch_ms_update<T, 5>(a, buf, num_sms, s); break;
+    case 6: dispatch_ms_update<T, 6>(a, buf, num_sms, s); break;
+    case 7: dispatch_ms_update<T, 7>(a, buf, num_sms, s); break;
+    default: throw Err{RAFEAST_ERR_INVALID_ARG};
+  }
+}
+
+template void launch_ms_init<float>(const CocgArgs<float>&, int, int, cudaStream_t);
+template void launch_ms_init<double>(const CocgArgs<double>&, int, int, cudaStream_t);
+template void launch_ms_update<float>(const CocgArgs<float>&, int, int, cudaStream_t);
+template void launch_ms_update<double>(const CocgArgs<double>&, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // plain SpMM variants
@@ -507,16 +734,6 @@ __global__ void __launch_bounds__(THREADS) k_spmm_real(int64_t n, const int32_t*
 // launchers
 // ---------------------------------------------------------------------------
 
-template <typename K>
-static int grid_x(K kernel, size_t smem, int num_sms, int64_t rows_needed_groups) {
-  int occ = 0;
-  RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, THREADS, smem));
-  if (occ < 1) occ = 1;
-  int64_t g = (int64_t)num_sms * occ;
-  if (g > rows_needed_groups) g = rows_needed_groups;
-  if (g < 1) g = 1;
-  return (int)g;
-}
 
 template <typename T, int NC, int MC>
 static void dispatch_dots_mc(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {

@@ -60,11 +60,13 @@ def knn8k():
     return lap, g, w, v
 
 
+@pytest.mark.parametrize("solver", [0, 1])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_knn8k_rafeast(lib, knn8k, prec):
+def test_knn8k_rafeast(lib, knn8k, prec, solver):
     lap, g, w, v = knn8k
     cfg = CF.CONFIGS["knn8k"]
     h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, solver)
     try:
         lib.rafeast_warmstart(h, g["lmin"], g["lmax"], cfg.m0, cfg.p, cfg.q, cfg.seed)
         p = lib.RAFEAST_FP64 if prec == "fp64" else lib.RAFEAST_MIXED

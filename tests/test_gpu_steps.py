@@ -192,13 +192,17 @@ def _filter_case():
     return lap, lmin, lmax
 
 
+@pytest.mark.parametrize("solver", [0, 1])
 @pytest.mark.parametrize("form", ["direct", "correction"])
 @pytest.mark.parametrize("nc,e", [(1, 1.0), (2, 1.0), (3, 0.5), (4, 1.0), (5, 0.3), (8, 1.0)])
-def test_filter_fp64(lib, form, nc, e):
+def test_filter_fp64(lib, form, nc, e, solver):
+    """solver 0: one COCG per shift; 1: multi-shift COCG (one seed recurrence
+    per column, the other shifts from its scalars)."""
     import torch
     lap, lmin, lmax = _filter_case()
     m0 = 11
     h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, solver)
     try:
         q0 = OF.random_start(lap.n, m0, 3)
         z, w = OQ.nodes(lmin, lmax, nc, e)
@@ -217,13 +221,15 @@ def test_filter_fp64(lib, form, nc, e):
         lib.rafeast_destroy(h)
 
 
+@pytest.mark.parametrize("solver", [0, 1])
 @pytest.mark.parametrize("form", ["direct", "correction"])
 @pytest.mark.parametrize("nc", [2, 4])
-def test_filter_mixed(lib, form, nc):
+def test_filter_mixed(lib, form, nc, solver):
     import torch
     lap, lmin, lmax = _filter_case()
     m0 = 11
     h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, solver)
     try:
         q0 = OF.random_start(lap.n, m0, 3)
         z, w = OQ.nodes(lmin, lmax, nc, 1.0)
@@ -306,15 +312,17 @@ def test_gather_kernels_match_oracle_stepwise(lib, mat, m0, nc):
         f32 = np.linalg.norm(_filter_complex64(A, q0, z, w, 12) - exp) / scale
         tol = max(5e-5, 2.0 * f32)
         errs = {}
-        for kern in (1, 2):
-            lib.rafeast_set_option(h, lib.RAFEAST_OPT_KERNEL, kern)
+        for kern in (1, 2, 3):
+            # 1 register gathers, 2 bulk-copy gathers, 3 multi-shift solver
+            lib.rafeast_set_option(h, lib.RAFEAST_OPT_KERNEL, 2 if kern == 2 else 1)
+            lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, 1 if kern == 3 else 0)
             Qt = torch.zeros_like(Q)
             prm = lib.make_params(lo, hi, m0, nc, 1.0, 0.0, 1e-10, 1, 12, lib.RAFEAST_MIXED,
                                   lib.RAFEAST_FORM_CORRECTION)
             info = lib.rafeast_filter(h, prm, Q, None, Qt)
             assert info.cocg_max_last == 12
             errs[kern] = np.linalg.norm(from_colmajor(Qt) - exp) / scale
-        assert errs[1] <= tol and errs[2] <= tol, (errs, f32)
+        assert errs[1] <= tol and errs[2] <= tol and errs[3] <= tol, (errs, f32)
     finally:
         lib.rafeast_destroy(h)
 
