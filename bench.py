@@ -318,6 +318,7 @@ def main():
                 "traffic": _traffic_per_launch(kern, key),
                 "algorithmic_bytes_per_launch": bytes_per, "ms_per_launch": ms_per,
                 "launches": int(launches_k),
+                "shapes": {"dots": prof.get("dots_shape"), "update": prof.get("update_shape")},
                 "other_kernel": {"kernel": "cocg_" + other,
                                  "achieved": (prof[f"{other}_bytes"] / max(prof[f"{other}_ms"], 1e-9))
                                  / 1e6,

@@ -546,57 +546,127 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
   a.scf = (ShiftCoef<T>*)(sc + o_scf);
   launch_ms_init<T>(a, m0, h->num_sms, h->stream);
   h->launches += 2;
-  int chunk = std::max(2, h->opt_chunk);
-  chunk += chunk & 1;
   const bool prof = h->opt_profile != 0;
-  std::vector<cudaEvent_t> evs;
-  if (prof) {
-    evs.resize(2 * chunk + 1);
-    for (auto& e : evs) RF_CUDA(cudaEventCreate(&e));
-  }
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  RF_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  g_capturing = true;
-  try {
-    for (int it = 0; it < chunk; ++it) {
-      if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * it], h->stream, cudaEventRecordExternal));
-      launch_cocg_dots<T>(a, 2, it & 1, h->num_sms, h->stream);
-      if (prof)
-        RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], h->stream, cudaEventRecordExternal));
-      launch_ms_update<T>(a, it & 1, h->num_sms, h->stream);
-    }
-    if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * chunk], h->stream, cudaEventRecordExternal));
-  } catch (...) {
-    g_capturing = false;
-    cudaStreamEndCapture(h->stream, &graph);
-    if (graph) cudaGraphDestroy(graph);
-    for (auto& e : evs) cudaEventDestroy(e);
-    throw;
-  }
-  g_capturing = false;
-  RF_CUDA(cudaStreamEndCapture(h->stream, &graph));
-  RF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  std::vector<float> tk;  // per executed step: dot ms, update ms (profiling)
   CocgCtl ctl;
-  const int max_replays = (prm.max_inner + 2) / chunk + 2;
-  int replays = 0;
-  std::vector<float> tk;
-  for (; replays < max_replays; ++replays) {
+  memset(&ctl, 0, sizeof(ctl));
+  // capture `steps` COCG steps with the given shapes; event nodes around each
+  // kernel when timing is wanted (the graph records them on every replay)
+  auto capture = [&](const CocgArgs<T>& ad, const CocgArgs<T>& au, int steps, bool timed,
+                     std::vector<cudaEvent_t>& evs, cudaGraphExec_t& exec) {
+    if (timed) {
+      evs.resize(2 * steps + 1);
+      for (auto& e : evs) RF_CUDA(cudaEventCreate(&e));
+    }
+    cudaGraph_t graph = nullptr;
+    RF_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
+    try {
+      for (int it = 0; it < steps; ++it) {
+        if (timed)
+          RF_CUDA(cudaEventRecordWithFlags(evs[2 * it], h->stream, cudaEventRecordExternal));
+        launch_cocg_dots<T>(ad, 2, it & 1, h->num_sms, h->stream);
+        if (timed)
+          RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], h->stream, cudaEventRecordExternal));
+        launch_ms_update<T>(au, it & 1, h->num_sms, h->stream);
+      }
+      if (timed)
+        RF_CUDA(cudaEventRecordWithFlags(evs[2 * steps], h->stream, cudaEventRecordExternal));
+    } catch (...) {
+      g_capturing = false;
+      cudaStreamEndCapture(h->stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    g_capturing = false;
+    RF_CUDA(cudaStreamEndCapture(h->stream, &graph));
+    RF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    RF_CUDA(cudaGraphDestroy(graph));
+  };
+  auto replay = [&](cudaGraphExec_t exec, int steps, bool timed, std::vector<cudaEvent_t>& evs,
+                    std::vector<float>* out) {
     RF_CUDA(cudaGraphLaunch(exec, h->stream));
     RF_CUDA(cudaMemcpyAsync(&ctl, a.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->stream));
     RF_CUDA(cudaStreamSynchronize(h->stream));
-    if (prof)
-      for (int it = 0; it < 2 * chunk; ++it) {
+    if (timed && out)
+      for (int it = 0; it < 2 * steps; ++it) {
         float ms = 0.f;
         RF_CUDA(cudaEventElapsedTime(&ms, evs[it], evs[it + 1]));
-        tk.push_back(ms);
+        out->push_back(ms);
       }
-    if (ctl.done) break;
+    h->launches += 2 * steps;
+    h->spmm_launches += 2 * steps;
+  };
+  // K10 autotuner: the dot and update kernels take their own (lanes, chunks)
+  // shape. Untuned, each candidate runs two real COCG steps (timed by graph
+  // event nodes) at the start of this solve; the fastest per kernel is kept
+  // for this handle. Shapes change only the work split, not the arithmetic.
+  CocgArgs<T> ad = a, au = a;
+  const int64_t key = ((int64_t)pairs << 20) | ((int64_t)ns << 4) | (fp64 ? 1 : 0);
+  const int cap = h->opt_cpl > 0 ? std::min(h->opt_cpl, ms_max_cpl(fp64)) : ms_max_cpl(fp64);
+  bool have = false;
+  for (auto& kv : h->tuned)
+    if (kv.first == key) {
+      ad.lanes = kv.second.dl;
+      ad.cpl = kv.second.dc;
+      au.lanes = kv.second.ul;
+      au.cpl = kv.second.uc;
+      have = true;
+    }
+  if (!have && h->opt_autotune && !h->opt_lanes && !h->opt_cpl) {
+    const int cand[][2] = {{32, 2}, {16, 2}, {16, 3}, {16, 4}, {8, 1}, {8, 2}, {8, 4}, {4, 2}};
+    float best_d = 1e30f, best_u = 1e30f;
+    for (auto& c : cand) {
+      if (ctl.done) break;
+      const int G = c[0], cpl = c[1];
+      if (cpl > cap) continue;
+      const int blocks = (pairs + G * cpl - 1) / (G * cpl);
+      if ((double)pairs / (blocks * G * cpl) < 0.5) continue;
+      CocgArgs<T> t = a;
+      t.lanes = G;
+      t.cpl = cpl;
+      std::vector<cudaEvent_t> evs;
+      cudaGraphExec_t exec = nullptr;
+      capture(t, t, 2, true, evs, exec);
+      std::vector<float> times;
+      replay(exec, 2, true, evs, &times);
+      RF_CUDA(cudaGraphExecDestroy(exec));
+      for (auto& e : evs) RF_CUDA(cudaEventDestroy(e));
+      tk.insert(tk.end(), times.begin(), times.end());
+      // second step of the pair: its kernels ran with every column active
+      // unless the solve already finished
+      const float td = std::min(times[0], times[2]), tu = std::min(times[1], times[3]);
+      if (td < best_d) {
+        best_d = td;
+        ad.lanes = G;
+        ad.cpl = cpl;
+      }
+      if (tu < best_u) {
+        best_u = tu;
+        au.lanes = G;
+        au.cpl = cpl;
+      }
+    }
+    Handle::Shape shp;
+    shp.dl = ad.lanes;
+    shp.dc = ad.cpl;
+    shp.ul = au.lanes;
+    shp.uc = au.cpl;
+    h->tuned.push_back(std::make_pair(key, shp));
   }
-  h->launches += 2 * chunk * (replays + 1);
-  h->spmm_launches += 2 * chunk * (replays + 1);
+  h->prof[6] = ad.lanes * 100 + ad.cpl;
+  h->prof[7] = au.lanes * 100 + au.cpl;
+  int chunk = std::max(2, h->opt_chunk);
+  chunk += chunk & 1;
+  std::vector<cudaEvent_t> evs;
+  cudaGraphExec_t exec = nullptr;
+  capture(ad, au, chunk, prof, evs, exec);
+  const int max_replays = (prm.max_inner + 2) / chunk + 2;
+  int replays = 0;
+  for (; replays < max_replays && !ctl.done; ++replays) {
+    replay(exec, chunk, prof, evs, &tk);
+  }
   RF_CUDA(cudaGraphExecDestroy(exec));
-  RF_CUDA(cudaGraphDestroy(graph));
   for (auto& e : evs) RF_CUDA(cudaEventDestroy(e));
   if (prof && ctl.done) {
     const int iters = std::min(ctl.iter, prm.max_inner + 1);
@@ -990,7 +1060,7 @@ int rafeast_profile(rafeast_t hh, int reset, double* out) {
   if (out)
     for (int t = 0; t < 8; ++t) out[t] = h->prof[t];
   if (reset)
-    for (int t = 0; t < 8; ++t) h->prof[t] = 0.0;
+    for (int t = 0; t < 6; ++t) h->prof[t] = 0.0;
   return RAFEAST_OK;
 }
 

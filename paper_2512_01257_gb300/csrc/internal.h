@@ -164,7 +164,13 @@ struct Handle {
   int opt_autotune = 1;
   int opt_lanes = 0;
   int opt_cpl = 0;     // cap on column chunks per lane (0: kernel maximum)
-  int opt_solver = 0;  // 0: COCG per shift, 1: multi-shift COCG
+  int opt_solver = 1;  // 0: COCG per shift, 1: multi-shift COCG (default)
+  // autotuned kernel shapes (lanes, chunks per lane) of the multi-shift
+  // kernels, keyed by (pairs, shifts, precision)
+  struct Shape {
+    int dl, dc, ul, uc;
+  };
+  std::vector<std::pair<int64_t, Shape>> tuned;
   int opt_profile = 0;
   int opt_kernel = 0;  // 0 auto, 1 register gathers, 2 bulk-copy gathers
   int opt_maxnz = 8;   // nonzeros per bulk-copy item

@@ -227,7 +227,8 @@ def rafeast_profile(h, reset=True):
     out = np.zeros(8)
     _check(load().rafeast_profile(h, int(reset), _ptr(out)), "rafeast_profile")
     return dict(dots_launches=out[0], dots_ms=out[1], dots_bytes=out[2],
-                update_launches=out[3], update_ms=out[4], update_bytes=out[5])
+                update_launches=out[3], update_ms=out[4], update_bytes=out[5],
+                dots_shape=int(out[6]), update_shape=int(out[7]))
 
 
 def rafeast_profile_history(h):
