@@ -306,8 +306,11 @@ def main():
 
     # roofline of the dominant COCG kernel (live CUDA-event times in the replays)
     peak, peak_kind = _peaks()
-    kern = "cocg_update" if prof["update_ms"] >= prof["dots_ms"] else "cocg_dots"
-    pre = "update" if kern == "cocg_update" else "dots"
+    # multi-shift COCG (default): seed dot kernel k_cocg_dots<.., 2, ..> and
+    # k_ms_update; names of the ncu summaries under profiles/
+    names = {"update": "ms_update", "dots": "ms_dots"}
+    pre = "update" if prof["update_ms"] >= prof["dots_ms"] else "dots"
+    kern = names[pre]
     launches_k = max(prof[f"{pre}_launches"], 1.0)
     bytes_per = prof[f"{pre}_bytes"] / launches_k
     ms_per = prof[f"{pre}_ms"] / launches_k
@@ -319,7 +322,7 @@ def main():
                 "algorithmic_bytes_per_launch": bytes_per, "ms_per_launch": ms_per,
                 "launches": int(launches_k),
                 "shapes": {"dots": prof.get("dots_shape"), "update": prof.get("update_shape")},
-                "other_kernel": {"kernel": "cocg_" + other,
+                "other_kernel": {"kernel": names[other],
                                  "achieved": (prof[f"{other}_bytes"] / max(prof[f"{other}_ms"], 1e-9))
                                  / 1e6,
                                  "ms_per_launch": prof[f"{other}_ms"] / max(prof[f"{other}_launches"], 1)},
