@@ -10,7 +10,10 @@ Eq. 1 defines the target: every eigenpair of A with eigenvalue in
 * ARPACK (``scipy.sparse.linalg.eigsh``) in shift-invert mode about a real
   shift, with a SuperLU factorisation in a symmetric minimum-degree order,
   for large sparse A (ARPACK is the library behind the RSpectra ground truth
-  of Section 5.1).
+  of Section 5.1);
+* ARPACK's implicitly restarted Lanczos on A itself (smallest algebraic
+  eigenvalues, no factorisation) for sparse graphs without geometric
+  structure, whose LU factors would fill in (stochastic block models).
 """
 from __future__ import annotations
 
@@ -87,6 +90,19 @@ def eigsh_smallest(a: sp.spmatrix, k: int, sigma: float = 0.0,
                   options=dict(SymmetricMode=True))
     op = sla.LinearOperator(a.shape, matvec=lu.solve, dtype=np.float64)
     w, v = sla.eigsh(a, k=k, sigma=sigma, which="LM", OPinv=op, tol=tol)
+    order = np.argsort(w)
+    return w[order], v[:, order]
+
+
+def eigsh_smallest_lanczos(a: sp.spmatrix, k: int, tol: float = 1e-12,
+                           seed: int = 0):
+    """k smallest eigenpairs of the symmetric A by ARPACK Lanczos (which =
+    'SA') with a seeded start vector; returns ascending values, vectors."""
+    a = sp.csr_matrix(a)
+    n = a.shape[0]
+    v0 = np.random.default_rng(seed).standard_normal(n)
+    ncv = min(n, max(4 * k, 60))
+    w, v = sla.eigsh(a, k=k, which="SA", tol=tol, ncv=ncv, v0=v0)
     order = np.argsort(w)
     return w[order], v[:, order]
 

@@ -65,6 +65,19 @@ def test_eigsh_matches_dense():
     assert np.linalg.norm(a @ v - v * w) < 1e-10
 
 
+def test_lanczos_matches_dense_on_sbm():
+    # a small stochastic block model: no geometric structure, the case the
+    # factorisation-free Lanczos routine serves; brute force decides
+    lap = G.sbm([120, 100, 130, 110], 20.0 / 115, 1.0 / 460, seed=9, shift=1e-3)
+    a = lap.scipy()
+    w, v = E.eigsh_smallest_lanczos(a, 12)
+    lam = np.linalg.eigvalsh(a.toarray())
+    assert np.allclose(w, lam[:12], rtol=1e-10, atol=1e-12)
+    assert np.linalg.norm(a @ v - v * w) < 1e-9
+    # the constant vector is the shifted Laplacian's eigenvector 1e-3
+    assert abs(w[0] - 1e-3) < 1e-12
+
+
 def test_sin_theta_metric():
     rng = np.random.default_rng(0)
     u, _ = np.linalg.qr(rng.standard_normal((50, 4)))

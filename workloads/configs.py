@@ -21,7 +21,9 @@ too, so every consumer reads the same numbers.
   inner solves as ``knn200k``.
 * ``sbm64``   batched RA-FEAST, mixed: 64 stochastic-block-model Laplacians
   + 1e-3 I, n log-uniform in [2000, 300000] (seed 4), 4..16 blocks,
-  p_in = 20/n_block, p_out = 1/n, k = blocks + 8, m0 = ceil(1.5 k), N_c=2.
+  p_in = 20/n_block, p_out = 1/n, k = blocks + 8, m0 = ceil(1.5 k), N_c=2;
+  the solver settings of ``knn200k`` (SBM_SOLVE), warmstart p=10, q=2 with
+  each instance's own seed.
 """
 from __future__ import annotations
 
@@ -80,6 +82,11 @@ def _cfgs():
 
 
 CONFIGS = _cfgs()
+
+
+# solver settings of every instance of the batched SBM sweep
+SBM_SOLVE = dict(nc=2, precision="mixed", solve_tol=1e-2, outer_tol=1e-11, form="correction",
+                 p=10, q=2, max_outer=40, max_inner=100)
 
 
 def sbm_instances(count: int = 64, seed: int = 4, n_lo: int = 2000,
