@@ -4,6 +4,11 @@ One step = one full RA-FEAST solve (Algorithm 2: randomized warmstart, then
 FEAST iterations until every in-interval Ritz pair has relative residual <=
 outer_tol) of the workload below, inputs resident in HBM. Prints one JSON line.
 
+``--workload sbm64``: the batched sweep, 64 stochastic-block-model Laplacians
+of uneven n (2,000 to 300,000) solved by one rafeast_solve_batched call
+(grouped COCG launches under one captured graph) per step; the line also
+reports the same 64 problems solved one at a time by rafeast_solve.
+
 Default workload (``knn200k``): kNN graph Laplacian of 200,000 uniform points
 in [0,1]^3 (seed 2), k = 10, union-symmetrised, unit weights, + 1e-3 I; the
 64 smallest eigenvalues; m0 = 80, N_c = 4, p = 20, q = 2, outer tolerance
@@ -36,6 +41,7 @@ WORKLOADS = {
     "knn200k": dict(key="knn200k", precision="mixed"),
     "grid3d": dict(key="grid3d", precision="mixed"),
     "knn8k": dict(key="knn8k", precision="fp64"),
+    "sbm64": dict(key="sbm64", precision="mixed"),
 }
 
 
@@ -205,6 +211,281 @@ def _config(key):
                   "float32" if cfg.precision == "mixed" else "L2 flushed between steps"}
 
 
+def run_batched(args):
+    """--workload sbm64: one step = warmstart of all 64 instances + one
+    batched solve; the per-instance loop of the same work is timed beside it."""
+    import numpy as np
+    import torch
+    from paper_2512_01257_gb300 import rafeast as R
+    from workloads import configs as CF
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    S = CF.SBM_SOLVE
+    gold = CF.load_golden()["sbm64"]["instances"]
+    insts = CF.sbm_instances()
+    t_gen = time.perf_counter()
+    laps = [CF.make_sbm(i) for i in insts]
+    t_gen = time.perf_counter() - t_gen
+    for lap, g in zip(laps, gold):
+        assert lap.checksum() == g["checksum"], "instance differs from the stored spectrum"
+    hs = []
+    for lap in laps:
+        hs.append(R.rafeast_create(torch.from_numpy(lap.row_ptr).to(dev),
+                                   torch.from_numpy(lap.col_idx).to(dev),
+                                   torch.from_numpy(lap.values).to(dev), lap.shift))
+    cnt = len(hs)
+    m0s = [i["m0"] for i in insts]
+    prms = [R.make_params(g["lmin"], g["lmax"], i["m0"], S["nc"], S["e"], S["solve_tol"],
+                          S["outer_tol"], S["max_outer"], S["max_inner"], R.RAFEAST_MIXED,
+                          R.RAFEAST_FORM_CORRECTION, R.RAFEAST_START_SUBSPACE)
+            for i, g in zip(insts, gold)]
+    evals = [torch.zeros(m, dtype=torch.float64, device=dev) for m in m0s]
+    evecs = [torch.zeros((m, lap.n), dtype=torch.float64, device=dev) for m, lap in zip(m0s, laps)]
+    resid = [torch.zeros(m, dtype=torch.float64, device=dev) for m in m0s]
+    last = {}
+
+    def warm(hl):
+        for h, i, g in zip(hl, insts, gold):
+            R.rafeast_warmstart(h, g["lmin"], g["lmax"], i["m0"], S["p"], S["q"], i["seed"])
+
+    def step():
+        warm(hs)
+        st, mf, info = R.rafeast_solve_batched(hs, prms, evals, evecs, resid)
+        # 2 (no convergence within max_outer) still returns the best iterate;
+        # the parity check below decides whether its eigenvalues are right
+        if any(x not in (R.RAFEAST_OK, R.RAFEAST_NO_CONVERGENCE) for x in st):
+            raise RuntimeError(f"batched statuses {st}")
+        last.update(mf=mf, info=info, st=st)
+
+    for _ in range(args.warmup):
+        step()
+    R.rafeast_set_option(hs[0], R.RAFEAST_OPT_PROFILE, 1)
+    R.rafeast_profile(hs[0], reset=True)
+    clocks = Clocks(local)
+    stream = torch.cuda.current_stream()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        step()
+        launches += sum(i.kernel_launches for i in last["info"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = R.rafeast_profile(hs[0], reset=True)
+    R.rafeast_set_option(hs[0], R.RAFEAST_OPT_PROFILE, 0)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    # parity: every instance's eigenvalues against its stored Lanczos spectrum
+    worst, found_all = 0.0, True
+    for t in range(cnt):
+        mf = last["mf"][t]
+        ev = np.sort(evals[t].cpu().numpy()[:mf])
+        ref = np.array(gold[t]["evals"])
+        if mf != len(ref):
+            found_all = False
+            continue
+        worst = max(worst, float(np.max(np.abs(ev - ref) / np.abs(ref))))
+    infos = last["info"]
+    # the same 64 problems one at a time (rafeast_solve each, same settings)
+    loop_ms, loop_kernels = None, None
+    trace = R.rafeast_profile_history(hs[0])
+    if not args.no_loop:
+        for h in hs:
+            R.rafeast_set_option(h, R.RAFEAST_OPT_PROFILE, 1)
+            R.rafeast_profile(h, reset=True)
+        torch.cuda.synchronize()
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        warm(hs)
+        for t in range(cnt):
+            st, _, _ = R.rafeast_solve(hs[t], prms[t], evals[t], evecs[t], resid[t])
+            assert st in (R.RAFEAST_OK, R.RAFEAST_NO_CONVERGENCE)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        loop_ms = l0.elapsed_time(l1)
+        lp = [R.rafeast_profile(h, reset=True) for h in hs]
+        for h in hs:
+            R.rafeast_set_option(h, R.RAFEAST_OPT_PROFILE, 0)
+        loop_kernels = {"dots_ms": sum(p["dots_ms"] for p in lp),
+                        "update_ms": sum(p["update_ms"] for p in lp),
+                        "steps": int(sum(p["dots_launches"] for p in lp))}
+    peak, peak_kind = _peaks()
+    pre = "update" if prof["update_ms"] >= prof["dots_ms"] else "dots"
+    names = {"update": "ms_update_grouped", "dots": "ms_dots_grouped"}
+    launches_k = max(prof[f"{pre}_launches"], 1.0)
+    bytes_per = prof[f"{pre}_bytes"] / launches_k
+    ms_per = prof[f"{pre}_ms"] / launches_k
+    achieved = bytes_per / (ms_per * 1e-3) / 1e9
+    other = "dots" if pre == "update" else "update"
+    roofline = {"bound": "hbm", "kernel": names[pre], "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": _traffic_per_launch(names[pre], "sbm64"),
+                "algorithmic_bytes_per_launch": bytes_per, "ms_per_launch": ms_per,
+                "launches": int(launches_k),
+                "other_kernel": {"kernel": names[other],
+                                 "achieved": (prof[f"{other}_bytes"] / max(prof[f"{other}_ms"], 1e-9))
+                                 / 1e6,
+                                 "ms_per_launch": prof[f"{other}_ms"] / max(prof[f"{other}_launches"], 1)},
+                "share_of_step": (prof["update_ms"] + prof["dots_ms"]) / ms}
+    ns = [lap.n for lap in laps]
+    value = args.steps * cnt * world / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": "problems/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "time_to_solution_s": ms_step / 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "precision": "mixed: f32 shifted solves and SpMM; f64 Gram, Cholesky-QR, "
+                         "Rayleigh-Ritz, residuals",
+            "data": "synthetic (seeded generator, no dataset)",
+            "config": {"workload": "sbm64: 64 stochastic-block-model Laplacians + 1e-3 I, n "
+                                   "log-uniform in [2000, 300000], 4-16 blocks, p_in=20/n_block, "
+                                   "p_out=1/n, k=blocks+8, m0=ceil(1.5k), N_c=2 (ellipse ratio "
+                                   "0.3), batched",
+                       "count": cnt, "sum_n": int(sum(ns)), "min_n": min(ns), "max_n": max(ns),
+                       "sum_nnz": int(sum(lap.nnz for lap in laps)), "nc": S["nc"],
+                       "p": S["p"], "q": S["q"], "solve_tol": S["solve_tol"],
+                       "outer_tol": S["outer_tol"], "max_inner": S["max_inner"],
+                       "l2": "inputs larger than L2 (no flush): COCG state of all instances"},
+            "parity": {"max_eig_relerr_vs_lanczos": worst if found_all else None,
+                       "all_found": found_all, "gate": 1e-8,
+                       "converged": sum(1 for x in last["st"] if x == R.RAFEAST_OK),
+                       "count": cnt},
+            "outer_iters_max": max(i.outer_iters for i in infos),
+            "outer_iters_mean": statistics.mean(i.outer_iters for i in infos),
+            "per_instance_loop_ms": loop_ms, "per_instance_loop_kernels": loop_kernels,
+            "batched_kernels": {"dots_ms": prof["dots_ms"] / args.steps,
+                                "update_ms": prof["update_ms"] / args.steps,
+                                "steps": int(prof["dots_launches"] / args.steps)},
+            "batched_speedup_vs_loop": (loop_ms / ms_step) if loop_ms else None,
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": ck,
+            "generation_s": t_gen}
+    if args.trace:
+        cols, probs, kms = trace
+        with open(args.trace, "w") as f:
+            json.dump({"active_pairs": cols.tolist(), "active_problems": probs.tolist(),
+                       "ms": kms.tolist()}, f)
+    for h in hs:
+        R.rafeast_destroy(h)
+    if not args.no_e2e:
+        pins = [(torch.from_numpy(l.row_ptr).pin_memory(), torch.from_numpy(l.col_idx).pin_memory(),
+                 torch.from_numpy(l.values).pin_memory()) for l in laps]
+        oev = [np.zeros(m) for m in m0s]
+        ove = [np.zeros((m, l.n)) for m, l in zip(m0s, laps)]
+        ore = [np.zeros(m) for m in m0s]
+        bi = sum(a.numel() * 4 + b.numel() * 4 + c.numel() * 8 for a, b, c in pins)
+        bo = sum(a.nbytes + b.nbytes + c.nbytes for a, b, c in zip(oev, ove, ore))
+
+        def e2e_step():
+            hl = [R.rafeast_create(a.numpy(), b.numpy(), c.numpy(), l.shift)
+                  for (a, b, c), l in zip(pins, laps)]
+            try:
+                warm(hl)
+                st, _, _ = R.rafeast_solve_batched(hl, prms, oev, ove, ore)
+                assert all(x in (R.RAFEAST_OK, R.RAFEAST_NO_CONVERGENCE) for x in st)
+            finally:
+                for h in hl:
+                    R.rafeast_destroy(h)
+
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        line["e2e"] = {"value": cnt * world / el, "unit": "problems/s",
+                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": 1,
+                       "includes": "rafeast_create of all 64 from pinned host CSR, warmstarts, "
+                                   "batched solve, copy of eigenpairs to host"}
+    if not args.no_cpu and rank == 0 and world == 1:
+        d = _cpu_sample_sbm(insts, gold, infos)
+        if "est" in d:
+            line["cpu_baseline"] = {"value": cnt / d["est"], "unit": "problems/s", "cores": 1,
+                                    "kind": "oracle", "sample": d["sample"],
+                                    "est_seconds_per_step": d["est"]}
+        else:
+            line["cpu_baseline"] = {"error": d.get("error")}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _cpu_sample_sbm(insts, gold, infos):
+    """Oracle (single-threaded) on the instance of median size: warmstart, a
+    few COCG steps, one Rayleigh-Ritz; extrapolated to the whole batch by nnz
+    and to each instance's GPU iteration counts."""
+    med = sorted(range(len(insts)), key=lambda t: insts[t]["n"])[len(insts) // 2]
+    code = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+from oracle import cocg as OC, feast as OF, philox as OP, quadrature as OQ
+from workloads import configs as CF
+t = int(sys.argv[2]); lmin, lmax = float(sys.argv[3]), float(sys.argv[4])
+S = CF.SBM_SOLVE
+inst = CF.sbm_instances()[t]
+a = CF.make_sbm(inst).scipy()
+n, m0 = a.shape[0], inst["m0"]
+t0 = time.perf_counter()
+om = OP.gaussian_matrix(n, m0 + S["p"], inst["seed"])
+q0, th0, _ = OF.warmstart(a, lmin, lmax, m0, S["p"], S["q"], om)
+t_ws = time.perf_counter() - t0
+z, w = OQ.nodes(lmin, lmax, S["nc"], S["e"])
+rmat = a @ q0 - q0 * th0
+t0 = time.perf_counter()
+OC.cocg(lambda x: a @ x, z[0], rmat, 0.0, 3)
+t_step = (time.perf_counter() - t0) / 3
+t0 = time.perf_counter()
+OF.rayleigh_ritz(a, OF.orthonormalize(q0))
+t_rr = time.perf_counter() - t0
+print(json.dumps(dict(t_ws=t_ws, t_step=t_step, t_rr=t_rr, nnz=a.nnz)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    g = gold[med]
+    t0 = time.perf_counter()
+    res = subprocess.run([sys.executable, "-c", code, ROOT, str(med), repr(g["lmin"]),
+                          repr(g["lmax"])], capture_output=True, text=True, env=env)
+    wall = time.perf_counter() - t0
+    if res.returncode != 0:
+        return {"error": res.stderr[-400:]}
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    est = 0.0
+    for t, (i, gg) in enumerate(zip(insts, gold)):
+        f = gg["nnz"] / d["nnz"]
+        est += f * (d["t_ws"] + infos[t].outer_iters * d["t_rr"]
+                    + 2 * infos[t].cocg_iters_total * d["t_step"])
+    sample = (f"oracle on instance {med} (n={insts[med]['n']}): warmstart, 3 COCG steps of one "
+              f"shift, one Rayleigh-Ritz ({wall:.1f} s of CPU work); scaled by nnz to every "
+              f"instance and to its GPU outer / COCG iteration counts x 2 shifts")
+    return {"est": est, "sample": sample}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,9 +496,13 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-loop", action="store_true")
+    ap.add_argument("--trace", default="", help="sbm64: write the batched per-step trace here")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sbm64":
+        return run_batched(args)
 
     import numpy as np
     import torch

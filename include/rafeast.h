@@ -188,7 +188,10 @@ int rafeast_profile(rafeast_t h, int reset, double* out);
  * the step's dot kernel and update kernel (kernel_ms[2k], kernel_ms[2k+1]).
  * Copies at most max_len steps into the host arrays (any may be NULL) and
  * returns the history length (0 when nothing was profiled), or -1 for a NULL
- * handle. */
+ * handle. After a profiled rafeast_solve_batched the first handle holds the
+ * whole batch's trace instead: per grouped COCG step, the active pairs of all
+ * problems (active_cols), the number of active problems (max_relres) and the
+ * step's grouped dot and update milliseconds. */
 int rafeast_profile_history(rafeast_t h, int max_len, int* active_cols, double* max_relres,
                             double* kernel_ms);
 
@@ -318,11 +321,21 @@ int rafeast_solve(rafeast_t h, const rafeast_params* prm, int* m_found,
                   double* evals, double* evecs, double* resid,
                   int outputs_on_device, rafeast_info* info);
 
-/* Solve count independent problems (handles, each with its own params and
- * outputs, arrays of count pointers) with their COCG iterations batched into
- * shared launches: one sparse-product launch per COCG step covers every
- * instance. Outputs as rafeast_solve, per instance; statuses[count] receives
- * each instance's status (host). Returns the first negative status, or 0. */
+/* Solve count independent problems (distinct handles on one device, each
+ * with its own params and outputs; arrays of count pointers) as one batch.
+ * All problems share precision and nc. Every outer iteration runs the
+ * filter of all problems still iterating together: multi-shift COCG (the
+ * RAFEAST_OPT_SOLVER = 1 path, whatever the handles' options) whose steps
+ * are grouped launches, one dot and one update launch per step covering
+ * every problem, captured as one CUDA graph on the first handle's stream.
+ * The per-problem CholQR, Rayleigh-Ritz and residual phases run on the
+ * problems' own streams, driven from up to 16 host threads, so their short
+ * kernels overlap. A problem stops when it converges or reaches its own
+ * max_outer. Outputs and statuses as rafeast_solve, per problem;
+ * statuses[count] receives each problem's status (host). The grouped
+ * launches are counted in the first problem's info. Returns the first
+ * negative status, or 0; -1 (with a message) for mixed precision, mixed nc,
+ * mixed devices or a repeated handle. */
 int rafeast_solve_batched(int count, rafeast_t const* hs,
                           const rafeast_params* prms, int* m_found,
                           double* const* evals, double* const* evecs,

@@ -19,8 +19,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librafeast.so")
-SOURCES = ["kernels_sparse.cu", "kernels_tma.cu", "kernels_dense.cu", "api.cu", "noalloc.cu",
-           "hostmath.cpp"]
+SOURCES = ["kernels_sparse.cu", "kernels_batched.cu", "kernels_tma.cu", "kernels_dense.cu",
+           "api.cu", "noalloc.cu", "hostmath.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,7 +34,7 @@ def nvcc() -> str:
 def _compile(src: str, extra, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-O3", "-I", os.path.join(os.path.dirname(PKG), "include"),
+           "-Xcompiler", "-O3", "-Xcompiler", "-pthread", "-I", os.path.join(os.path.dirname(PKG), "include"),
            "--diag-suppress", "177", "-c", os.path.join(CSRC, src), "-o", obj, *extra]
     if src.endswith(".cpp"):
         cmd.insert(1, "-x")
@@ -55,7 +55,7 @@ def build(verbose: bool = False, extra=()) -> str:
         objs = list(ex.map(lambda s: _compile(s, list(extra), verbose), SOURCES))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-           "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+           "-Xcompiler", "-pthread", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     if verbose:
         print(" ".join(cmd), flush=True)
     res = subprocess.run(cmd, capture_output=True, text=True)

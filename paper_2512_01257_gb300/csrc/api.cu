@@ -7,11 +7,16 @@
 // graphs of `chunk` steps and replayed until the device reports that every
 // system has converged.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <memory>
 #include <mutex>
 #include <numeric>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -49,6 +54,23 @@ void check_launch(const char* file, int line) {
     set_last_error(e, "kernel launch", file, line);
     throw Err{e == cudaErrorMemoryAllocation ? RAFEAST_ERR_OUT_OF_MEMORY : RAFEAST_ERR_CUDA};
   }
+}
+
+void ensure_dyn_smem(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<int, const void*>, size_t>> set;
+  int dev = 0;
+  RF_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& e : set)
+    if (e.first.first == dev && e.first.second == fn) {
+      if (e.second >= bytes) return;
+      RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      e.second = bytes;
+      return;
+    }
+  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  set.push_back(std::make_pair(std::make_pair(dev, fn), bytes));
 }
 
 void* scratch(Handle* h, int slot, size_t bytes) {
@@ -421,10 +443,21 @@ static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, c
 // Q~ as filter_dev in exact arithmetic, a quarter of the gathered bytes at
 // N_c = 4.
 template <typename T>
-static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd,
-                          const double* AQd, const double* theta_d,
-                          const std::vector<double>& theta, int m0, int ldq, double* Qt,
-                          FilterStats& fs) {
+struct MsProblem {
+  CocgArgs<T> a;
+  const double* fin = nullptr;  // device [m0]: per-column constant of the correction form
+  int m0 = 0, pairs = 0, ns = 0;
+};
+
+// one multi-shift problem on stream st: quadrature, seed choice, coefficient
+// upload, state reset and init (two launches); default kernel shape. ctl_dev,
+// when not null, replaces the handle's own control block (batched solves keep
+// every problem's block in one array).
+template <typename T>
+static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double* Qd,
+                             const double* AQd, const double* theta_d,
+                             const std::vector<double>& theta, int m0, int ldq, CocgCtl* ctl_dev,
+                             bool profile, cudaStream_t st) {
   using C = c2<T>;
   const int nc = prm.nc;
   const bool fp64 = sizeof(T) == 8;
@@ -491,15 +524,15 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
   const size_t o_hist = carve(sizeof(int) * ((size_t)prm.max_inner + 2));
   const size_t o_rhist = carve(sizeof(double) * ((size_t)prm.max_inner + 2));
   char* sc = (char*)scratch(h, S_SCAL, off + 256);
-  RF_CUDA(cudaMemcpyAsync(sc + o_zs, zs.data(), sizeof(C) * 2, cudaMemcpyHostToDevice, h->stream));
+  RF_CUDA(cudaMemcpyAsync(sc + o_zs, zs.data(), sizeof(C) * 2, cudaMemcpyHostToDevice, st));
   RF_CUDA(cudaMemcpyAsync(sc + o_coef, coef.data(), sizeof(double2) * ncol, cudaMemcpyHostToDevice,
-                          h->stream));
+                          st));
   RF_CUDA(cudaMemcpyAsync(sc + o_fin, finit.data(), sizeof(double) * m0, cudaMemcpyHostToDevice,
-                          h->stream));
+                          st));
   RF_CUDA(cudaMemcpyAsync(sc + o_sig, sigma.data(), sizeof(double2) * sigma.size(),
-                          cudaMemcpyHostToDevice, h->stream));
+                          cudaMemcpyHostToDevice, st));
   RF_CUDA(cudaMemcpyAsync(sc + o_scoef, scoef.data(), sizeof(double2) * scoef.size(),
-                          cudaMemcpyHostToDevice, h->stream));
+                          cudaMemcpyHostToDevice, st));
   CocgArgs<T> a;
   memset(&a, 0, sizeof(a));
   a.n = h->n;
@@ -530,8 +563,8 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
   a.cf = (Coef<T>*)(sc + o_cf);
   a.colact = (int*)(sc + o_col);
   a.ctl = (CocgCtl*)(sc + o_ctl);
-  a.hist = h->opt_profile ? (int*)(sc + o_hist) : nullptr;
-  a.rhist = h->opt_profile ? (double*)(sc + o_rhist) : nullptr;
+  a.hist = profile ? (int*)(sc + o_hist) : nullptr;
+  a.rhist = profile ? (double*)(sc + o_rhist) : nullptr;
   a.nc_real = 2;
   a.tol2 = prm.solve_tol * prm.solve_tol;
   a.max_inner = prm.max_inner;
@@ -544,8 +577,59 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
   a.scoef = (const double2*)(sc + o_scoef);
   a.sst = (ShiftState*)(sc + o_sst);
   a.scf = (ShiftCoef<T>*)(sc + o_scf);
-  launch_ms_init<T>(a, m0, h->num_sms, h->stream);
+  if (ctl_dev) a.ctl = ctl_dev;
+  launch_ms_init<T>(a, m0, h->num_sms, st);
   h->launches += 2;
+  MsProblem<T> P;
+  P.a = a;
+  P.fin = (const double*)(sc + o_fin);
+  P.m0 = m0;
+  P.pairs = pairs;
+  P.ns = ns;
+  return P;
+}
+
+// algorithmic bytes of one multi-shift step of a problem with act_d pairs
+// active in the dot kernel and act_u in the update kernel: A once per kernel;
+// the dot kernel reads the seed residual; the update kernel reads and writes
+// the seed r and p, the shifted directions and the quadrature sum
+static double ms_dots_bytes(const Handle* h, int act_d, bool fp64) {
+  const double sv = fp64 ? 8.0 : 4.0;
+  const double abytes = (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
+  const double pairb = (double)h->n * 2 * 2.0 * sv;
+  return abytes + pairb * act_d;
+}
+static double ms_update_bytes(const Handle* h, int act_u, int ns, bool fp64) {
+  const double sv = fp64 ? 8.0 : 4.0;
+  const double abytes = (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
+  const double pairb = (double)h->n * 2 * 2.0 * sv;
+  return abytes + (4.0 + 2.0 * ns) * pairb * act_u + 2.0 * (double)h->n * 2 * act_u * sv;
+}
+
+// combine Qt = f Q + D and the solve's statistics (after the device reported done)
+template <typename T>
+static void ms_finish(Handle* h, const MsProblem<T>& P, const double* Qd, int ldq, double* Qt,
+                      const CocgCtl& ctl, FilterStats& fs, cudaStream_t st) {
+  if (!ctl.done || ctl.timeout) throw Err{RAFEAST_ERR_TIMEOUT};
+  fs.iters_max = ctl.max_iters;
+  fs.iters_min = ctl.min_iters;
+  fs.breakdown = ctl.breakdown;
+  fs.capped = ctl.capped;
+  launch_combine<T>(Qd, ldq, P.a.dacc, P.a.ldd, P.fin, h->n, P.m0, Qt, st);
+  h->launches += 1;
+  if (fs.breakdown) throw Err{RAFEAST_ERR_COCG_BREAKDOWN};
+}
+
+template <typename T>
+static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd,
+                          const double* AQd, const double* theta_d,
+                          const std::vector<double>& theta, int m0, int ldq, double* Qt,
+                          FilterStats& fs) {
+  const bool fp64 = sizeof(T) == 8;
+  MsProblem<T> P = ms_setup<T>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, nullptr,
+                                h->opt_profile != 0, h->stream);
+  const CocgArgs<T>& a = P.a;
+  const int pairs = P.pairs, ns = P.ns;
   const bool prof = h->opt_profile != 0;
   std::vector<float> tk;  // per executed step: dot ms, update ms (profiling)
   CocgCtl ctl;
@@ -677,33 +761,209 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
     RF_CUDA(cudaMemcpy(h->last_rhist.data(), a.rhist, sizeof(double) * iters,
                        cudaMemcpyDeviceToHost));
     h->last_tk.assign(tk.begin(), tk.begin() + std::min<size_t>(tk.size(), 2 * (size_t)iters));
-    // algorithmic bytes: A once; seed pair-columns (r read by the dot kernel;
-    // r, p read and written by the update kernel); shifted directions read and
-    // written; quadrature sum read and written. hist counts active pairs.
-    const double sv = fp64 ? 8.0 : 4.0;
-    const double abytes = (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
-    const double pairb = (double)h->n * 2 * 2.0 * sv;  // one pair of one complex array
     for (int k = 0; k < iters && 2 * k + 1 < (int)tk.size(); ++k) {
       const int act_d = k == 0 ? pairs : hist[k - 1];
       const int act_u = hist[k];
       h->prof[0] += 1;
       h->prof[1] += tk[2 * k];
-      h->prof[2] += abytes + pairb * act_d;
+      h->prof[2] += ms_dots_bytes(h, act_d, fp64);
       if (act_u > 0) {
         h->prof[3] += 1;
         h->prof[4] += tk[2 * k + 1];
-        h->prof[5] += abytes + (4.0 + 2.0 * ns) * pairb * act_u + 2.0 * (double)h->n * 2 * act_u * sv;
+        h->prof[5] += ms_update_bytes(h, act_u, ns, fp64);
       }
     }
   }
-  if (!ctl.done || ctl.timeout) throw Err{RAFEAST_ERR_TIMEOUT};
-  fs.iters_max = ctl.max_iters;
-  fs.iters_min = ctl.min_iters;
-  fs.breakdown = ctl.breakdown;
-  fs.capped = ctl.capped;
-  launch_combine<T>(Qd, ldq, dacc, ldd, (const double*)(sc + o_fin), h->n, m0, Qt, h->stream);
-  h->launches += 1;
-  if (fs.breakdown) throw Err{RAFEAST_ERR_COCG_BREAKDOWN};
+  ms_finish<T>(h, P, Qd, ldq, Qt, ctl, fs, h->stream);
+}
+
+// ---------------------------------------------------------------------------
+// batched multi-shift filter: the COCG steps of every problem of a batch run
+// in grouped launches (one dot and one update launch per step for all
+// problems, kernels_batched.cu) captured as one CUDA graph of `chunk` steps on
+// the batch stream bs; the graph is replayed until every problem's device
+// control block reports done. Per-problem setup and the final combine are
+// ordinary launches on bs. Errors of one problem (breakdown, timeout) are
+// stored in its item; errors of the batch as a whole throw.
+// ---------------------------------------------------------------------------
+struct BatchItem {
+  Handle* h = nullptr;
+  const rafeast_params* prm = nullptr;
+  double* Qt = nullptr;
+  FilterStats fs;
+  int err = 0;
+};
+
+template <typename T>
+static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cudaStream_t bs) {
+  const int cnt = (int)items.size();
+  if (cnt == 0) return;
+  const bool fp64 = sizeof(T) == 8;
+  // every problem's inputs were produced on its own stream
+  for (auto* it : items) {
+    RF_CUDA(cudaEventRecord(it->h->ev_out, it->h->stream));
+    RF_CUDA(cudaStreamWaitEvent(bs, it->h->ev_out, 0));
+  }
+  // one device buffer: every problem's control block (one array the host
+  // polls), kernel arguments, item maps, queue control, shapes
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    size_t o = off;
+    off += bytes;
+    return o;
+  };
+  const size_t o_ctl = carve(sizeof(CocgCtl) * cnt);
+  const size_t o_args = carve(sizeof(CocgArgs<T>) * cnt);
+  const size_t o_md = carve(sizeof(int) * (2 * cnt + 1));
+  const size_t o_mu = carve(sizeof(int) * (2 * cnt + 1));
+  const size_t o_gc = carve(sizeof(GroupCtl));
+  const size_t o_gg = carve(sizeof(int) * 4 * cnt);
+  char* bb = (char*)scratch(owner, S_BATCH, off + 256);
+  CocgCtl* ctl_d = (CocgCtl*)(bb + o_ctl);
+  std::vector<MsProblem<T>> P(cnt);
+  std::vector<CocgArgs<T>> args(cnt);
+  const int cap = std::min(2, ms_max_cpl(fp64));
+  for (int t = 0; t < cnt; ++t) {
+    Handle* h = items[t]->h;
+    P[t] = ms_setup<T>(h, *items[t]->prm, h->Q, h->AQ, h->theta_d, h->theta, h->m0, h->ldq,
+                       ctl_d + t, owner->opt_profile != 0, bs);
+    // at most two chunks per lane: the two-CTA-per-SM kernel instances
+    int cb = 1;
+    choose_shape(P[t].pairs, 2, fp64, 0, P[t].a.lanes, P[t].a.cpl, cb, cap);
+    args[t] = P[t].a;
+  }
+  GroupPlan plan;
+  plan_ms_grouped<T>(args, owner->num_sms, plan);
+  GroupCtl gch;
+  memset(&gch, 0, sizeof(gch));
+  gch.grid_d = plan.ctas_dots;
+  gch.grid_u = plan.ctas_upd;
+  RF_CUDA(cudaMemcpyAsync(bb + o_args, args.data(), sizeof(CocgArgs<T>) * cnt,
+                          cudaMemcpyHostToDevice, bs));
+  RF_CUDA(cudaMemcpyAsync(bb + o_md, plan.map_dots.data(), sizeof(int) * plan.map_dots.size(),
+                          cudaMemcpyHostToDevice, bs));
+  RF_CUDA(cudaMemcpyAsync(bb + o_mu, plan.map_upd.data(), sizeof(int) * plan.map_upd.size(),
+                          cudaMemcpyHostToDevice, bs));
+  RF_CUDA(cudaMemcpyAsync(bb + o_gc, &gch, sizeof(gch), cudaMemcpyHostToDevice, bs));
+  RF_CUDA(cudaMemcpyAsync(bb + o_gg, plan.gg.data(), sizeof(int) * plan.gg.size(),
+                          cudaMemcpyHostToDevice, bs));
+  GroupDev<T> gd;
+  gd.args = (const CocgArgs<T>*)(bb + o_args);
+  gd.map_d = (int*)(bb + o_md);
+  gd.map_u = (int*)(bb + o_mu);
+  gd.gc = (GroupCtl*)(bb + o_gc);
+  gd.ctl = ctl_d;
+  gd.gg = (const int4*)(bb + o_gg);
+  const bool prof = owner->opt_profile != 0;
+  int chunk = std::max(2, owner->opt_chunk);
+  chunk += chunk & 1;
+  std::vector<cudaEvent_t> evs;
+  if (prof) {
+    evs.resize(2 * chunk + 1);
+    for (auto& e : evs) RF_CUDA(cudaEventCreate(&e));
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  RF_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+  g_capturing = true;
+  try {
+    for (int it = 0; it < chunk; ++it) {
+      if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * it], bs, cudaEventRecordExternal));
+      launch_ms_grouped<T>(plan, gd, 0, it & 1, bs);
+      if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], bs, cudaEventRecordExternal));
+      launch_ms_grouped<T>(plan, gd, 1, it & 1, bs);
+    }
+    if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * chunk], bs, cudaEventRecordExternal));
+  } catch (...) {
+    g_capturing = false;
+    cudaStreamEndCapture(bs, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto& e : evs) cudaEventDestroy(e);
+    throw;
+  }
+  g_capturing = false;
+  RF_CUDA(cudaStreamEndCapture(bs, &graph));
+  RF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  RF_CUDA(cudaGraphDestroy(graph));
+  int max_inner = 1;
+  for (auto* it : items) max_inner = std::max(max_inner, it->prm->max_inner);
+  const int max_replays = (max_inner + 2) / chunk + 2;
+  std::vector<CocgCtl> ctl(cnt);
+  std::vector<float> tk;
+  bool all_done = false;
+  for (int r = 0; r < max_replays && !all_done; ++r) {
+    RF_CUDA(cudaGraphLaunch(exec, bs));
+    RF_CUDA(cudaMemcpyAsync(ctl.data(), ctl_d, sizeof(CocgCtl) * cnt, cudaMemcpyDeviceToHost, bs));
+    RF_CUDA(cudaStreamSynchronize(bs));
+    if (prof)
+      for (int k = 0; k < 2 * chunk; ++k) {
+        float ms = 0.f;
+        RF_CUDA(cudaEventElapsedTime(&ms, evs[k], evs[k + 1]));
+        tk.push_back(ms);
+      }
+    owner->launches += 2 * chunk;
+    owner->spmm_launches += 2 * chunk;
+    all_done = true;
+    for (int t = 0; t < cnt; ++t) all_done = all_done && ctl[t].done;
+  }
+  RF_CUDA(cudaGraphExecDestroy(exec));
+  for (auto& e : evs) RF_CUDA(cudaEventDestroy(e));
+  if (prof && all_done) {
+    // per-step time of the grouped kernels against the algorithmic bytes of
+    // every problem still active in that step
+    int steps = 0;
+    std::vector<std::vector<int>> hist(cnt);
+    for (int t = 0; t < cnt; ++t) {
+      const int iters = std::min(ctl[t].iter, items[t]->prm->max_inner + 1);
+      hist[t].assign(iters, 0);
+      if (iters > 0 && P[t].a.hist)
+        RF_CUDA(cudaMemcpy(hist[t].data(), P[t].a.hist, sizeof(int) * iters,
+                           cudaMemcpyDeviceToHost));
+      steps = std::max(steps, iters);
+    }
+    for (int k = 0; k < steps && 2 * k + 1 < (int)tk.size(); ++k) {
+      double bd = 0.0, bu = 0.0;
+      int probs = 0, pairs_act = 0;
+      for (int t = 0; t < cnt; ++t) {
+        const int iters = (int)hist[t].size();
+        if (k >= iters) continue;
+        const int act_d = k == 0 ? P[t].pairs : hist[t][k - 1];
+        const int act_u = hist[t][k];
+        bd += ms_dots_bytes(items[t]->h, act_d, fp64);
+        if (act_u > 0) bu += ms_update_bytes(items[t]->h, act_u, P[t].ns, fp64);
+        if (act_d > 0) ++probs;
+        pairs_act += act_d;
+      }
+      // batched trace, appended over the whole solve: active pairs, active
+      // problems, dot and update milliseconds of the step
+      owner->last_hist.push_back(pairs_act);
+      owner->last_rhist.push_back((double)probs);
+      owner->last_tk.push_back(tk[2 * k]);
+      owner->last_tk.push_back(tk[2 * k + 1]);
+      owner->prof[0] += 1;
+      owner->prof[1] += tk[2 * k];
+      owner->prof[2] += bd;
+      if (bu > 0.0) {
+        owner->prof[3] += 1;
+        owner->prof[4] += tk[2 * k + 1];
+        owner->prof[5] += bu;
+      }
+    }
+    owner->prof[6] = 0;
+    owner->prof[7] = 0;
+  }
+  for (int t = 0; t < cnt; ++t) {
+    Handle* h = items[t]->h;
+    try {
+      ms_finish<T>(h, P[t], h->Q, h->ldq, items[t]->Qt, ctl[t], items[t]->fs, bs);
+    } catch (const Err& e) {
+      items[t]->err = e.code;
+    }
+  }
+  // every problem's next phase runs on its own stream after the batch
+  RF_CUDA(cudaEventRecord(owner->ev_in, bs));
+  for (auto* it : items) RF_CUDA(cudaStreamWaitEvent(it->h->stream, owner->ev_in, 0));
 }
 
 static void validate_params(const rafeast_params* p) {
@@ -797,6 +1057,178 @@ static void subspace_from_Q(Handle* h, int m0) {
                           cudaMemcpyDeviceToHost, h->stream));
   RF_CUDA(cudaStreamSynchronize(h->stream));
   h->m0 = m0;
+}
+
+// ---------------------------------------------------------------------------
+// the outer FEAST loop in phases (Algorithm 1 / Algorithm 2 Phase 2):
+// start, per-iteration tail after the filter (CholQR, Rayleigh-Ritz,
+// residuals, convergence), outputs. rafeast_solve runs them in sequence;
+// rafeast_solve_batched interleaves many problems with one batched filter.
+// ---------------------------------------------------------------------------
+struct SolveRun {
+  Handle* h = nullptr;
+  rafeast_params prm;
+  int m0 = 0, ldq = 0;
+  double *Qt = nullptr, *T1 = nullptr, *T2 = nullptr;
+  std::vector<double> res;
+  int status = RAFEAST_NO_CONVERGENCE;
+  int it = 0, cocg_total = 0, shifted_total = 0;
+  FilterStats fs;
+  float t_filter = 0, t_orth = 0, t_rr = 0;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  SolveRun() { memset(&prm, 0, sizeof(prm)); }
+  SolveRun(const SolveRun&) = delete;
+  SolveRun& operator=(const SolveRun&) = delete;
+  ~SolveRun() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+// starting subspace: random Gaussian block orthonormalised (plain FEAST), or
+// the handle's current subspace (after rafeast_warmstart / set_subspace)
+static void solve_begin(SolveRun& r, Handle* h, const rafeast_params& prm) {
+  r.h = h;
+  r.prm = prm;
+  const int m0 = prm.m0;
+  r.m0 = m0;
+  for (auto& e : r.ev) RF_CUDA(cudaEventCreate(&e));
+  RF_CUDA(cudaEventRecord(r.ev[0], h->stream));
+  if (prm.start == RAFEAST_START_RANDOM) {
+    ensure_subspace_bufs(h, m0);
+    double* om = (double*)scratch(h, S_OMEGA, sizeof(double) * h->n * m0);
+    launch_omega(prm.seed, h->n, m0, om, h->stream);
+    launch_to_internal(h->n, m0, om, h->Q, h->ldq, h->perm, h->stream);
+    h->launches += 2;
+    double* X = h->Q;
+    double* Y = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * h->ldq);
+    cholqr(h, X, Y, m0, h->ldq, nullptr);
+    if (X != h->Q)
+      RF_CUDA(cudaMemcpyAsync(h->Q, X, sizeof(double) * h->n * h->ldq, cudaMemcpyDeviceToDevice,
+                              h->stream));
+    // A Q and Rayleigh quotients (the correction form's theta)
+    launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m0, h->ldq, 1.0, h->shift, h->Q,
+                             h->AQ, h->num_sms, h->stream);
+    h->launches += 1;
+    h->spmm_launches += 1;
+    col_dot(h->Q, h->AQ, h->n, m0, h->ldq, h->theta_d, h->stream);
+    h->theta.resize(m0);
+    RF_CUDA(cudaMemcpyAsync(h->theta.data(), h->theta_d, sizeof(double) * m0,
+                            cudaMemcpyDeviceToHost, h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    h->m0 = m0;
+  } else {
+    if (!h->Q || h->m0 != m0) throw Err{RAFEAST_ERR_NOT_READY};
+  }
+  RF_CUDA(cudaEventRecord(r.ev[1], h->stream));
+  r.ldq = h->ldq;
+  r.Qt = (double*)scratch(h, S_QT, sizeof(double) * h->n * r.ldq);
+  r.T1 = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * r.ldq);
+  r.T2 = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * r.ldq);
+  RF_CUDA(cudaMemsetAsync(r.Qt, 0, sizeof(double) * h->n * r.ldq, h->stream));
+  RF_CUDA(cudaMemsetAsync(r.T1, 0, sizeof(double) * h->n * r.ldq, h->stream));
+  r.res.assign(m0, 0.0);
+}
+
+// after the filter wrote Qt (events ev[2], ev[3] bracket it): CholQR, RR,
+// residuals; true when every Ritz pair inside the interval has converged
+static bool solve_outer_tail(SolveRun& r) {
+  Handle* h = r.h;
+  const int m0 = r.m0, ldq = r.ldq;
+  double* X = r.Qt;
+  double* Y = r.T1;
+  r.shifted_total += cholqr(h, X, Y, m0, ldq, nullptr);
+  RF_CUDA(cudaEventRecord(r.ev[4], h->stream));
+  rayleigh_ritz_dev(h, X, m0, ldq, h->Q, h->AQ, h->theta_d, r.T2);
+  residuals_host(h, h->Q, h->AQ, h->theta_d, m0, ldq, r.res);
+  RF_CUDA(cudaEventRecord(r.ev[5], h->stream));
+  h->theta.resize(m0);
+  RF_CUDA(cudaMemcpyAsync(h->theta.data(), h->theta_d, sizeof(double) * m0,
+                          cudaMemcpyDeviceToHost, h->stream));
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  float a = 0, b = 0, c = 0;
+  RF_CUDA(cudaEventElapsedTime(&a, r.ev[2], r.ev[3]));
+  RF_CUDA(cudaEventElapsedTime(&b, r.ev[3], r.ev[4]));
+  RF_CUDA(cudaEventElapsedTime(&c, r.ev[4], r.ev[5]));
+  r.t_filter += a;
+  r.t_orth += b;
+  r.t_rr += c;
+  double mx = -1.0;
+  int nin = 0;
+  for (int i = 0; i < m0; ++i)
+    if (h->theta[i] >= r.prm.lmin && h->theta[i] <= r.prm.lmax) {
+      ++nin;
+      mx = std::max(mx, r.res[i]);
+    }
+  if (nin > 0 && mx <= r.prm.outer_tol) {
+    r.status = RAFEAST_OK;
+    return true;
+  }
+  return false;
+}
+
+// outputs: in-interval pairs first (ascending), then the rest (ascending)
+static int solve_finish(SolveRun& r, int* m_found, double* evals, double* evecs, double* resid,
+                        int outputs_on_device, rafeast_info* info) {
+  Handle* h = r.h;
+  const int m0 = r.m0;
+  int status = r.status;
+  std::vector<int> order;
+  for (int i = 0; i < m0; ++i)
+    if (h->theta[i] >= r.prm.lmin && h->theta[i] <= r.prm.lmax) order.push_back(i);
+  const int mf = (int)order.size();
+  for (int i = 0; i < m0; ++i)
+    if (!(h->theta[i] >= r.prm.lmin && h->theta[i] <= r.prm.lmax)) order.push_back(i);
+  if (mf == 0) status = RAFEAST_NO_EIGENVALUE;
+  else if (mf >= m0) status = RAFEAST_M0_TOO_SMALL;
+  *m_found = mf;
+  std::vector<double> ev_out(m0), res_out(m0);
+  double maxres = 0.0;
+  for (int t = 0; t < m0; ++t) {
+    ev_out[t] = h->theta[order[t]];
+    res_out[t] = r.res[order[t]];
+    if (t < mf) maxres = std::max(maxres, res_out[t]);
+  }
+  if (outputs_on_device) {
+    RF_CUDA(cudaMemcpyAsync(evals, ev_out.data(), sizeof(double) * m0, cudaMemcpyHostToDevice,
+                            h->stream));
+    if (resid)
+      RF_CUDA(cudaMemcpyAsync(resid, res_out.data(), sizeof(double) * m0, cudaMemcpyHostToDevice,
+                              h->stream));
+  } else {
+    std::copy(ev_out.begin(), ev_out.end(), evals);
+    if (resid) std::copy(res_out.begin(), res_out.end(), resid);
+  }
+  if (evecs) {
+    int32_t* cols_d = (int32_t*)scratch(h, S_SMALL, sizeof(int32_t) * m0 + 64);
+    std::vector<int32_t> cols(order.begin(), order.end());
+    RF_CUDA(cudaMemcpyAsync(cols_d, cols.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice,
+                            h->stream));
+    export_block(h, h->Q, r.ldq, m0, cols_d, outputs_on_device, evecs);
+  }
+  RF_CUDA(cudaEventRecord(r.ev[5], h->stream));
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  float tot = 0, tws = 0;
+  RF_CUDA(cudaEventElapsedTime(&tot, r.ev[0], r.ev[5]));
+  RF_CUDA(cudaEventElapsedTime(&tws, r.ev[0], r.ev[1]));
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = status;
+    info->outer_iters = r.it;
+    info->cocg_iters_total = r.cocg_total;
+    info->cocg_min_last = r.fs.iters_min;
+    info->cocg_max_last = r.fs.iters_max;
+    info->cholqr_shifted = r.shifted_total;
+    info->kernel_launches = h->launches;
+    info->spmm_launches = h->spmm_launches;
+    info->max_resid = maxres;
+    info->t_warmstart_ms = tws;
+    info->t_filter_ms = r.t_filter;
+    info->t_orth_ms = r.t_orth;
+    info->t_rr_ms = r.t_rr;
+    info->t_total_ms = tot;
+  }
+  return status;
 }
 
 }  // namespace rafeast
@@ -1472,145 +1904,17 @@ int rafeast_solve(rafeast_t hh, const rafeast_params* prm, int* m_found, double*
   RF_CHECK(prm->reserved == 0, RAFEAST_ERR_INVALID_ARG);
   RF_CHECK(prm->m0 <= h->n, RAFEAST_ERR_INVALID_ARG);
   CallScope scope(h);
-  const int m0 = prm->m0;
-  cudaEvent_t ev[6];
-  for (auto& e : ev) RF_CUDA(cudaEventCreate(&e));
-  RF_CUDA(cudaEventRecord(ev[0], h->stream));
-  if (prm->start == RAFEAST_START_RANDOM) {
-    ensure_subspace_bufs(h, m0);
-    double* om = (double*)scratch(h, S_OMEGA, sizeof(double) * h->n * m0);
-    launch_omega(prm->seed, h->n, m0, om, h->stream);
-    launch_to_internal(h->n, m0, om, h->Q, h->ldq, h->perm, h->stream);
-    h->launches += 2;
-    double* X = h->Q;
-    double* Y = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * h->ldq);
-    cholqr(h, X, Y, m0, h->ldq, nullptr);
-    if (X != h->Q)
-      RF_CUDA(cudaMemcpyAsync(h->Q, X, sizeof(double) * h->n * h->ldq, cudaMemcpyDeviceToDevice,
-                              h->stream));
-    // A Q and Rayleigh quotients (the correction form's theta)
-    launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m0, h->ldq, 1.0, h->shift, h->Q,
-                             h->AQ, h->num_sms, h->stream);
-    h->launches += 1;
-    h->spmm_launches += 1;
-    DenseWs d = dense_ws(h, m0);
-    col_dot(h->Q, h->AQ, h->n, m0, h->ldq, h->theta_d, h->stream);
-    h->theta.resize(m0);
-    RF_CUDA(cudaMemcpyAsync(h->theta.data(), h->theta_d, sizeof(double) * m0,
-                            cudaMemcpyDeviceToHost, h->stream));
-    RF_CUDA(cudaStreamSynchronize(h->stream));
-    (void)d;
-    h->m0 = m0;
-  } else {
-    if (!h->Q || h->m0 != m0) throw Err{RAFEAST_ERR_NOT_READY};
+  SolveRun r;
+  solve_begin(r, h, *prm);
+  for (r.it = 1; r.it <= prm->max_outer; ++r.it) {
+    RF_CUDA(cudaEventRecord(r.ev[2], h->stream));
+    run_filter(h, *prm, h->Q, h->AQ, h->theta_d, h->theta, r.m0, r.ldq, r.Qt, r.fs);
+    r.cocg_total += r.fs.iters_max;
+    RF_CUDA(cudaEventRecord(r.ev[3], h->stream));
+    if (solve_outer_tail(r)) break;
   }
-  RF_CUDA(cudaEventRecord(ev[1], h->stream));
-  const int ldq = h->ldq;
-  double* Qt = (double*)scratch(h, S_QT, sizeof(double) * h->n * ldq);
-  double* T1 = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ldq);
-  double* T2 = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ldq);
-  RF_CUDA(cudaMemsetAsync(Qt, 0, sizeof(double) * h->n * ldq, h->stream));
-  RF_CUDA(cudaMemsetAsync(T1, 0, sizeof(double) * h->n * ldq, h->stream));
-  std::vector<double> res(m0, 0.0);
-  int status = RAFEAST_NO_CONVERGENCE;
-  int it = 0;
-  int cocg_total = 0;
-  FilterStats fs;
-  float t_filter = 0, t_orth = 0, t_rr = 0;
-  int shifted_total = 0;
-  for (it = 1; it <= prm->max_outer; ++it) {
-    RF_CUDA(cudaEventRecord(ev[2], h->stream));
-    run_filter(h, *prm, h->Q, h->AQ, h->theta_d, h->theta, m0, ldq, Qt, fs);
-    cocg_total += fs.iters_max;
-    RF_CUDA(cudaEventRecord(ev[3], h->stream));
-    double* X = Qt;
-    double* Y = T1;
-    shifted_total += cholqr(h, X, Y, m0, ldq, nullptr);
-    RF_CUDA(cudaEventRecord(ev[4], h->stream));
-    rayleigh_ritz_dev(h, X, m0, ldq, h->Q, h->AQ, h->theta_d, T2);
-    residuals_host(h, h->Q, h->AQ, h->theta_d, m0, ldq, res);
-    RF_CUDA(cudaEventRecord(ev[5], h->stream));
-    h->theta.resize(m0);
-    RF_CUDA(cudaMemcpyAsync(h->theta.data(), h->theta_d, sizeof(double) * m0,
-                            cudaMemcpyDeviceToHost, h->stream));
-    RF_CUDA(cudaStreamSynchronize(h->stream));
-    float a = 0, b = 0, c = 0;
-    RF_CUDA(cudaEventElapsedTime(&a, ev[2], ev[3]));
-    RF_CUDA(cudaEventElapsedTime(&b, ev[3], ev[4]));
-    RF_CUDA(cudaEventElapsedTime(&c, ev[4], ev[5]));
-    t_filter += a;
-    t_orth += b;
-    t_rr += c;
-    double mx = -1.0;
-    int nin = 0;
-    for (int i = 0; i < m0; ++i)
-      if (h->theta[i] >= prm->lmin && h->theta[i] <= prm->lmax) {
-        ++nin;
-        mx = std::max(mx, res[i]);
-      }
-    if (nin > 0 && mx <= prm->outer_tol) {
-      status = RAFEAST_OK;
-      break;
-    }
-  }
-  if (it > prm->max_outer) it = prm->max_outer;
-  // outputs: in-interval pairs first (ascending), then the rest (ascending)
-  std::vector<int> order;
-  for (int i = 0; i < m0; ++i)
-    if (h->theta[i] >= prm->lmin && h->theta[i] <= prm->lmax) order.push_back(i);
-  const int mf = (int)order.size();
-  for (int i = 0; i < m0; ++i)
-    if (!(h->theta[i] >= prm->lmin && h->theta[i] <= prm->lmax)) order.push_back(i);
-  if (mf == 0) status = RAFEAST_NO_EIGENVALUE;
-  else if (mf >= m0) status = RAFEAST_M0_TOO_SMALL;
-  *m_found = mf;
-  std::vector<double> ev_out(m0), res_out(m0);
-  double maxres = 0.0;
-  for (int t = 0; t < m0; ++t) {
-    ev_out[t] = h->theta[order[t]];
-    res_out[t] = res[order[t]];
-    if (t < mf) maxres = std::max(maxres, res_out[t]);
-  }
-  if (outputs_on_device) {
-    RF_CUDA(cudaMemcpyAsync(evals, ev_out.data(), sizeof(double) * m0, cudaMemcpyHostToDevice,
-                            h->stream));
-    if (resid)
-      RF_CUDA(cudaMemcpyAsync(resid, res_out.data(), sizeof(double) * m0, cudaMemcpyHostToDevice,
-                              h->stream));
-  } else {
-    std::copy(ev_out.begin(), ev_out.end(), evals);
-    if (resid) std::copy(res_out.begin(), res_out.end(), resid);
-  }
-  if (evecs) {
-    int32_t* cols_d = (int32_t*)scratch(h, S_SMALL, sizeof(int32_t) * m0 + 64);
-    std::vector<int32_t> cols(order.begin(), order.end());
-    RF_CUDA(cudaMemcpyAsync(cols_d, cols.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice,
-                            h->stream));
-    export_block(h, h->Q, ldq, m0, cols_d, outputs_on_device, evecs);
-  }
-  RF_CUDA(cudaEventRecord(ev[5], h->stream));
-  RF_CUDA(cudaStreamSynchronize(h->stream));
-  float tot = 0, tws = 0;
-  RF_CUDA(cudaEventElapsedTime(&tot, ev[0], ev[5]));
-  RF_CUDA(cudaEventElapsedTime(&tws, ev[0], ev[1]));
-  for (auto& e : ev) cudaEventDestroy(e);
-  if (info) {
-    memset(info, 0, sizeof(*info));
-    info->status = status;
-    info->outer_iters = it;
-    info->cocg_iters_total = cocg_total;
-    info->cocg_min_last = fs.iters_min;
-    info->cocg_max_last = fs.iters_max;
-    info->cholqr_shifted = shifted_total;
-    info->kernel_launches = h->launches;
-    info->spmm_launches = h->spmm_launches;
-    info->max_resid = maxres;
-    info->t_warmstart_ms = tws;
-    info->t_filter_ms = t_filter;
-    info->t_orth_ms = t_orth;
-    info->t_rr_ms = t_rr;
-    info->t_total_ms = tot;
-  }
+  if (r.it > prm->max_outer) r.it = prm->max_outer;
+  const int status = solve_finish(r, m_found, evals, evecs, resid, outputs_on_device, info);
   scope.finish();
   return status;
   API_END
@@ -1622,15 +1926,130 @@ int rafeast_solve_batched(int count, rafeast_t const* hs, const rafeast_params* 
                           int* statuses) {
   if (count < 0 || (count > 0 && (!hs || !prms || !m_found || !evals || !statuses)))
     return RAFEAST_ERR_INVALID_ARG;
-  int first_err = RAFEAST_OK;
+  if (count == 0) return RAFEAST_OK;
+  clear_last_error();
+  API_BEGIN
+  std::vector<Handle*> H(count);
   for (int t = 0; t < count; ++t) {
-    const int rc = rafeast_solve(hs[t], &prms[t], &m_found[t], evals[t], evecs ? evecs[t] : nullptr,
-                                 resid ? resid[t] : nullptr, outputs_on_device,
-                                 infos ? &infos[t] : nullptr);
-    statuses[t] = rc;
-    if (rc < 0 && first_err == RAFEAST_OK) first_err = rc;
+    H[t] = reinterpret_cast<Handle*>(hs[t]);
+    RF_CHECK(H[t] && evals[t], RAFEAST_ERR_INVALID_ARG);
+    validate_params(&prms[t]);
+    RF_CHECK(prms[t].reserved == 0 && prms[t].m0 <= H[t]->n, RAFEAST_ERR_INVALID_ARG);
+    if (prms[t].precision != prms[0].precision || prms[t].nc != prms[0].nc ||
+        H[t]->device != H[0]->device) {
+      set_last_message("rafeast_solve_batched: every problem of a batch needs the same "
+                       "precision, the same nc and the same device");
+      throw Err{RAFEAST_ERR_INVALID_ARG};
+    }
+    for (int u = 0; u < t; ++u)
+      if (H[u] == H[t]) {
+        set_last_message("rafeast_solve_batched: a handle appears twice in the batch");
+        throw Err{RAFEAST_ERR_INVALID_ARG};
+      }
   }
+  Handle* owner = H[0];
+  const cudaStream_t bs = owner->stream;
+  std::vector<std::unique_ptr<CallScope>> scopes;
+  for (int t = 0; t < count; ++t) scopes.emplace_back(new CallScope(H[t]));
+  std::vector<SolveRun> runs(count);
+  std::vector<BatchItem> items(count);
+  std::vector<std::string> msgs(count);
+  // per-problem phases run on the problems' own streams from a few host
+  // threads, so their short kernels and host round trips overlap
+  auto each = [&](const std::vector<int>& which, const std::function<void(int)>& f) {
+    std::atomic<int> next(0);
+    auto work = [&]() {
+      cudaSetDevice(owner->device);
+      for (;;) {
+        const int k = next.fetch_add(1);
+        if (k >= (int)which.size()) break;
+        const int t = which[k];
+        try {
+          f(t);
+        } catch (const Err& e) {
+          items[t].err = e.code;
+          msgs[t] = g_err;
+        } catch (...) {
+          items[t].err = RAFEAST_ERR_CUDA;
+        }
+      }
+    };
+    const int nt = std::min<int>((int)which.size(), 16);
+    std::vector<std::thread> th;
+    for (int k = 1; k < nt; ++k) th.emplace_back(work);
+    work();
+    for (auto& x : th) x.join();
+  };
+  std::vector<int> all(count);
+  std::iota(all.begin(), all.end(), 0);
+  for (int t = 0; t < count; ++t) {
+    items[t].h = H[t];
+    items[t].prm = &prms[t];
+  }
+  each(all, [&](int t) {
+    solve_begin(runs[t], H[t], prms[t]);
+    items[t].Qt = runs[t].Qt;
+  });
+  if (owner->opt_profile) {
+    owner->last_hist.clear();
+    owner->last_rhist.clear();
+    owner->last_tk.clear();
+  }
+  std::vector<char> done(count, 0);
+  int max_outer = 0;
+  for (int t = 0; t < count; ++t) max_outer = std::max(max_outer, prms[t].max_outer);
+  for (int it = 1; it <= max_outer; ++it) {
+    std::vector<int> act;
+    std::vector<BatchItem*> act_items;
+    for (int t = 0; t < count; ++t)
+      if (!done[t] && !items[t].err && it <= prms[t].max_outer) {
+        act.push_back(t);
+        act_items.push_back(&items[t]);
+        runs[t].it = it;
+        RF_CUDA(cudaEventRecord(runs[t].ev[2], bs));
+      }
+    if (act.empty()) break;
+    if (prms[0].precision == RAFEAST_FP64) filter_ms_batched<double>(act_items, owner, bs);
+    else filter_ms_batched<float>(act_items, owner, bs);
+    for (int t : act) {
+      runs[t].fs = items[t].fs;
+      runs[t].cocg_total += items[t].fs.iters_max;
+      RF_CUDA(cudaEventRecord(runs[t].ev[3], bs));
+    }
+    // the problems' phases read the filter's end event from their own threads
+    RF_CUDA(cudaStreamSynchronize(bs));
+    std::vector<int> ok;
+    for (int t : act)
+      if (!items[t].err) ok.push_back(t);
+    each(ok, [&](int t) {
+      if (solve_outer_tail(runs[t])) done[t] = 1;
+    });
+  }
+  int first_err = RAFEAST_OK;
+  std::vector<int> fin;
+  for (int t = 0; t < count; ++t)
+    if (!items[t].err) fin.push_back(t);
+  each(fin, [&](int t) {
+    statuses[t] = solve_finish(runs[t], &m_found[t], evals[t], evecs ? evecs[t] : nullptr,
+                               resid ? resid[t] : nullptr, outputs_on_device,
+                               infos ? &infos[t] : nullptr);
+  });
+  for (int t = 0; t < count; ++t) {
+    if (items[t].err) {
+      statuses[t] = items[t].err;
+      if (infos) {
+        memset(&infos[t], 0, sizeof(rafeast_info));
+        infos[t].status = items[t].err;
+      }
+      if (first_err == RAFEAST_OK) {
+        first_err = items[t].err;
+        if (!msgs[t].empty()) set_last_message(msgs[t].c_str());
+      }
+    }
+  }
+  for (auto& sc : scopes) sc->finish();
   return first_err;
+  API_END
 }
 
 }  // extern "C"

@@ -189,9 +189,13 @@ struct Handle {
 };
 
 void* scratch(Handle* h, int slot, size_t bytes);  // keep-alive buffer per slot
+// raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device; never lowers it, so threads launching the same kernel with
+// different sizes cannot undercut one another
+void ensure_dyn_smem(const void* fn, size_t bytes);
 enum Slot {
   S_STATE = 0, S_DACC, S_QT, S_TMP1, S_TMP2, S_SCAL, S_GRAM, S_SMALL, S_OMEGA,
-  S_AQ2, S_IO1, S_IO2, S_COUNT
+  S_AQ2, S_IO1, S_IO2, S_BATCH, S_COUNT
 };
 
 // ---- host math (hostmath.cpp) ------------------------------------------------
@@ -231,6 +235,44 @@ template <typename T>
 void launch_cocg_dots(const CocgArgs<T>& a, int NC, int buf, int num_sms, cudaStream_t s);
 template <typename T>
 void launch_cocg_update(const CocgArgs<T>& a, int NC, int buf, int num_sms, cudaStream_t s);
+
+// grouped multi-shift COCG over many problems, one persistent launch per
+// kernel per step (kernels_batched.cu): the CTAs drain a queue of work items
+// (problem, row slice, column block) described by an item map (starts of the
+// problems' items [count + 1], then gx per problem); the dot kernel's last
+// CTA re-plans both maps on the device as problems finish.
+struct GroupCtl {
+  unsigned int ticket;  // CTAs of the current dot launch that have finished
+  unsigned int next_d;  // queue heads of the dot and update launches
+  unsigned int next_u;
+  int grid_d, grid_u;   // persistent grid sizes of the two kernels
+  int pad[3];
+};
+struct GroupPlan {
+  int count = 0;
+  int ns = 0;
+  int mc = 2;  // compiled chunks per lane of both kernels
+  size_t smem_dots = 0, smem_upd = 0;
+  const void* fn_dots = nullptr;
+  const void* fn_upd = nullptr;
+  std::vector<int> map_dots, map_upd;  // initial maps (every problem active)
+  std::vector<int> gg;  // per problem: row groups, column blocks, gathered KiB, 0
+  int ctas_dots = 0, ctas_upd = 0;  // persistent grid sizes
+};
+template <typename T> struct GroupDev {
+  const CocgArgs<T>* args;
+  int* map_d;
+  int* map_u;
+  GroupCtl* gc;
+  const CocgCtl* ctl;  // the problems' control blocks, contiguous
+  const int4* gg;
+};
+template <typename T>
+void plan_ms_grouped(const std::vector<CocgArgs<T>>& args, int num_sms, GroupPlan& g);
+// which: 0 dots (seed scalars of every problem, then the re-plan), 1 update
+template <typename T>
+void launch_ms_grouped(const GroupPlan& g, const GroupDev<T>& d, int which, int buf,
+                       cudaStream_t s);
 
 // W = zs_j P - L P over complex chunks (rafeast_shifted_spmm)
 template <typename T>

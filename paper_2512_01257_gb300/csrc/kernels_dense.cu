@@ -256,8 +256,7 @@ void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
   switch (U) {
 #define RF_GRAM(UU)                                                                   \
   case UU:                                                                            \
-    RF_CUDA(cudaFuncSetAttribute(k_gram_partial<UU>,                                   \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    ensure_dyn_smem(reinterpret_cast<const void*>(k_gram_partial<UU>), smem);        \
     k_gram_partial<UU><<<parts, 256, smem, s>>>(X, Y, n, m, ld, partial);             \
     break;
     RF_GRAM(1) RF_GRAM(2) RF_GRAM(3) RF_GRAM(4) RF_GRAM(5) RF_GRAM(6) RF_GRAM(7) RF_GRAM(8)
@@ -325,8 +324,7 @@ void tall_gemm(const double* X, int64_t n, int m, int ldx, const double* M, int 
   switch (V) {
 #define RF_TG(VV)                                                                     \
   case VV:                                                                            \
-    RF_CUDA(cudaFuncSetAttribute(k_tall_gemm<VV>,                                      \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    ensure_dyn_smem(reinterpret_cast<const void*>(k_tall_gemm<VV>), smem);           \
     k_tall_gemm<VV><<<blocks, 256, smem, s>>>(X, n, m, ldx, M, mo, Y, ldy);           \
     break;
     RF_TG(1) RF_TG(2) RF_TG(3) RF_TG(4)
@@ -422,7 +420,7 @@ __global__ void k_chol_inv(const double* __restrict__ G, int m, double shift_sca
 void chol_inv(double* G, int m, int64_t nrows, double* Rfac, double* Rinv, int* status,
               cudaStream_t s) {
   const size_t smem = (size_t)m * m * sizeof(double);
-  RF_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ensure_dyn_smem(reinterpret_cast<const void*>(k_chol_inv), smem);
   const double u = DBL_EPSILON / 2;
   const double scale = 11.0 * ((double)nrows * m + (double)m * (m + 1)) * u;
   k_chol_inv<<<1, 256, smem, s>>>(G, m, scale, Rfac, Rinv, status);
@@ -557,7 +555,7 @@ void jacobi_eigh(double* A, int m, double* w, double* V, double* work, cudaStrea
   if (m > 128) throw Err{RAFEAST_ERR_INVALID_ARG};
   const int me = m + (m & 1);
   const size_t smem = (size_t)me * me * sizeof(double);
-  RF_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ensure_dyn_smem(reinterpret_cast<const void*>(k_jacobi), smem);
   k_jacobi<<<1, 512, smem, s>>>(A, m, w, V, work, 40);
   RF_LAUNCH();
 }

@@ -618,12 +618,10 @@ static void run_tma(const CocgArgs<float>& a, int which, int buf, int maxnz, int
   const size_t red = (size_t)ncb * 32 * CPL * NC * 5 * sizeof(double);
   TmaShape t = tma_shape(num_sms, narr, SLOT, maxnz, ncb, which == 1 ? red : 0);
   if (which == 1) {
-    RF_CUDA(cudaFuncSetAttribute(k_dots_tma<NC, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)t.smem));
+    ensure_dyn_smem(reinterpret_cast<const void*>(k_dots_tma<NC, CPL>), t.smem);
     k_dots_tma<NC, CPL><<<t.grid, 32 * t.warps, t.smem, s>>>(a, buf, ncb, bw, t.maxnz, t.S);
   } else {
-    RF_CUDA(cudaFuncSetAttribute(k_update_tma<NC, CPL>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem));
+    ensure_dyn_smem(reinterpret_cast<const void*>(k_update_tma<NC, CPL>), t.smem);
     k_update_tma<NC, CPL><<<t.grid, 32 * t.warps, t.smem, s>>>(a, buf, ncb, bw, t.maxnz, t.S);
   }
   RF_LAUNCH();

@@ -22,8 +22,8 @@ too, so every consumer reads the same numbers.
 * ``sbm64``   batched RA-FEAST, mixed: 64 stochastic-block-model Laplacians
   + 1e-3 I, n log-uniform in [2000, 300000] (seed 4), 4..16 blocks,
   p_in = 20/n_block, p_out = 1/n, k = blocks + 8, m0 = ceil(1.5 k), N_c=2;
-  the solver settings of ``knn200k`` (SBM_SOLVE), warmstart p=10, q=2 with
-  each instance's own seed.
+  half-ellipse ratio e = 0.3, inner solves as ``knn200k``, outer tolerance
+  1e-10 (SBM_SOLVE), warmstart p=10, q=2 with each instance's own seed.
 """
 from __future__ import annotations
 
@@ -84,9 +84,15 @@ def _cfgs():
 CONFIGS = _cfgs()
 
 
-# solver settings of every instance of the batched SBM sweep
-SBM_SOLVE = dict(nc=2, precision="mixed", solve_tol=1e-2, outer_tol=1e-11, form="correction",
-                 p=10, q=2, max_outer=40, max_inner=100)
+# solver settings of every instance of the batched SBM sweep. The intervals
+# end inside the dense low edge of these spectra, so at N_c = 2 the filter's
+# contraction is poor on a circle (e = 1: 0.65-0.89 per outer iteration on
+# sampled instances; the oracle needs 186 iterations on instance 8). The
+# flatter ellipse of FEAST's Hermitian default (ratio 0.3) brings it to
+# 0.38-0.72 (67 iterations on instance 8). A 1e-10 residual bounds the
+# eigenvalue error far below the 1e-8 gate (the error enters squared).
+SBM_SOLVE = dict(nc=2, e=0.3, precision="mixed", solve_tol=1e-2, outer_tol=1e-10,
+                 form="correction", p=10, q=2, max_outer=150, max_inner=100)
 
 
 def sbm_instances(count: int = 64, seed: int = 4, n_lo: int = 2000,
