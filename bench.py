@@ -343,6 +343,8 @@ def run_batched(args):
                 "traffic": _traffic_per_launch(names[pre], "sbm64"),
                 "algorithmic_bytes_per_launch": bytes_per, "ms_per_launch": ms_per,
                 "launches": int(launches_k),
+                "shapes": {"dots": prof.get("dots_shape"), "update": prof.get("update_shape"),
+                           "note": "lanes*100+chunks, 0 = per-problem default"},
                 "other_kernel": {"kernel": names[other],
                                  "achieved": (prof[f"{other}_bytes"] / max(prof[f"{other}_ms"], 1e-9))
                                  / 1e6,

@@ -795,7 +795,8 @@ struct BatchItem {
 };
 
 template <typename T>
-static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cudaStream_t bs) {
+static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cudaStream_t bs,
+                              int64_t sig) {
   const int cnt = (int)items.size();
   if (cnt == 0) return;
   const bool fp64 = sizeof(T) == 8;
@@ -805,7 +806,7 @@ static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cud
     RF_CUDA(cudaStreamWaitEvent(bs, it->h->ev_out, 0));
   }
   // one device buffer: every problem's control block (one array the host
-  // polls), kernel arguments, item maps, queue control, shapes
+  // polls), the two kernels' arguments, item maps and shapes, queue control
   size_t off = 0;
   auto carve = [&](size_t bytes) {
     off = (off + 255) & ~(size_t)255;
@@ -814,101 +815,175 @@ static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cud
     return o;
   };
   const size_t o_ctl = carve(sizeof(CocgCtl) * cnt);
-  const size_t o_args = carve(sizeof(CocgArgs<T>) * cnt);
+  const size_t o_ad = carve(sizeof(CocgArgs<T>) * cnt);
+  const size_t o_au = carve(sizeof(CocgArgs<T>) * cnt);
   const size_t o_md = carve(sizeof(int) * (2 * cnt + 1));
   const size_t o_mu = carve(sizeof(int) * (2 * cnt + 1));
   const size_t o_gc = carve(sizeof(GroupCtl));
-  const size_t o_gg = carve(sizeof(int) * 4 * cnt);
+  const size_t o_ggd = carve(sizeof(int) * 4 * cnt);
+  const size_t o_ggu = carve(sizeof(int) * 4 * cnt);
   char* bb = (char*)scratch(owner, S_BATCH, off + 256);
   CocgCtl* ctl_d = (CocgCtl*)(bb + o_ctl);
   std::vector<MsProblem<T>> P(cnt);
-  std::vector<CocgArgs<T>> args(cnt);
-  const int cap = std::min(2, ms_max_cpl(fp64));
   for (int t = 0; t < cnt; ++t) {
     Handle* h = items[t]->h;
     P[t] = ms_setup<T>(h, *items[t]->prm, h->Q, h->AQ, h->theta_d, h->theta, h->m0, h->ldq,
                        ctl_d + t, owner->opt_profile != 0, bs);
-    // at most two chunks per lane: the two-CTA-per-SM kernel instances
-    int cb = 1;
-    choose_shape(P[t].pairs, 2, fp64, 0, P[t].a.lanes, P[t].a.cpl, cb, cap);
-    args[t] = P[t].a;
   }
-  GroupPlan plan;
-  plan_ms_grouped<T>(args, owner->num_sms, plan);
-  GroupCtl gch;
-  memset(&gch, 0, sizeof(gch));
-  gch.grid_d = plan.ctas_dots;
-  gch.grid_u = plan.ctas_upd;
-  RF_CUDA(cudaMemcpyAsync(bb + o_args, args.data(), sizeof(CocgArgs<T>) * cnt,
-                          cudaMemcpyHostToDevice, bs));
-  RF_CUDA(cudaMemcpyAsync(bb + o_md, plan.map_dots.data(), sizeof(int) * plan.map_dots.size(),
-                          cudaMemcpyHostToDevice, bs));
-  RF_CUDA(cudaMemcpyAsync(bb + o_mu, plan.map_upd.data(), sizeof(int) * plan.map_upd.size(),
-                          cudaMemcpyHostToDevice, bs));
-  RF_CUDA(cudaMemcpyAsync(bb + o_gc, &gch, sizeof(gch), cudaMemcpyHostToDevice, bs));
-  RF_CUDA(cudaMemcpyAsync(bb + o_gg, plan.gg.data(), sizeof(int) * plan.gg.size(),
-                          cudaMemcpyHostToDevice, bs));
   GroupDev<T> gd;
-  gd.args = (const CocgArgs<T>*)(bb + o_args);
+  gd.args_d = (const CocgArgs<T>*)(bb + o_ad);
+  gd.args_u = (const CocgArgs<T>*)(bb + o_au);
   gd.map_d = (int*)(bb + o_md);
   gd.map_u = (int*)(bb + o_mu);
   gd.gc = (GroupCtl*)(bb + o_gc);
   gd.ctl = ctl_d;
-  gd.gg = (const int4*)(bb + o_gg);
-  const bool prof = owner->opt_profile != 0;
-  int chunk = std::max(2, owner->opt_chunk);
-  chunk += chunk & 1;
-  std::vector<cudaEvent_t> evs;
-  if (prof) {
-    evs.resize(2 * chunk + 1);
-    for (auto& e : evs) RF_CUDA(cudaEventCreate(&e));
-  }
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  RF_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
-  g_capturing = true;
-  try {
-    for (int it = 0; it < chunk; ++it) {
-      if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * it], bs, cudaEventRecordExternal));
-      launch_ms_grouped<T>(plan, gd, 0, it & 1, bs);
-      if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], bs, cudaEventRecordExternal));
-      launch_ms_grouped<T>(plan, gd, 1, it & 1, bs);
-    }
-    if (prof) RF_CUDA(cudaEventRecordWithFlags(evs[2 * chunk], bs, cudaEventRecordExternal));
-  } catch (...) {
-    g_capturing = false;
-    cudaStreamEndCapture(bs, &graph);
-    if (graph) cudaGraphDestroy(graph);
-    for (auto& e : evs) cudaEventDestroy(e);
-    throw;
-  }
-  g_capturing = false;
-  RF_CUDA(cudaStreamEndCapture(bs, &graph));
-  RF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-  RF_CUDA(cudaGraphDestroy(graph));
-  int max_inner = 1;
-  for (auto* it : items) max_inner = std::max(max_inner, it->prm->max_inner);
-  const int max_replays = (max_inner + 2) / chunk + 2;
-  std::vector<CocgCtl> ctl(cnt);
-  std::vector<float> tk;
-  bool all_done = false;
-  for (int r = 0; r < max_replays && !all_done; ++r) {
-    RF_CUDA(cudaGraphLaunch(exec, bs));
-    RF_CUDA(cudaMemcpyAsync(ctl.data(), ctl_d, sizeof(CocgCtl) * cnt, cudaMemcpyDeviceToHost, bs));
-    RF_CUDA(cudaStreamSynchronize(bs));
-    if (prof)
-      for (int k = 0; k < 2 * chunk; ++k) {
-        float ms = 0.f;
-        RF_CUDA(cudaEventElapsedTime(&ms, evs[k], evs[k + 1]));
-        tk.push_back(ms);
+  gd.gg_d = (const int4*)(bb + o_ggd);
+  gd.gg_u = (const int4*)(bb + o_ggu);
+  // (lanes, chunks) of a kernel: 0 = each problem's own default (at most two
+  // chunks per lane, the two-CTA-per-SM instances), else one shape for all
+  auto shaped = [&](int G, int cpl) {
+    std::vector<CocgArgs<T>> v(cnt);
+    for (int t = 0; t < cnt; ++t) {
+      v[t] = P[t].a;
+      if (G == 0) {
+        int cb = 1;
+        choose_shape(P[t].pairs, 2, fp64, 0, v[t].lanes, v[t].cpl, cb,
+                     std::min(2, ms_max_cpl(fp64)));
+      } else {
+        v[t].lanes = G;
+        v[t].cpl = cpl;
       }
-    owner->launches += 2 * chunk;
-    owner->spmm_launches += 2 * chunk;
-    all_done = true;
-    for (int t = 0; t < cnt; ++t) all_done = all_done && ctl[t].done;
+    }
+    return v;
+  };
+  GroupPlan plan;
+  // upload the arguments, maps and shapes of one shape choice (the device
+  // has finished every earlier replay: each was synchronised)
+  auto prepare = [&](const std::vector<CocgArgs<T>>& ad, const std::vector<CocgArgs<T>>& au) {
+    plan = GroupPlan();
+    plan_ms_grouped<T>(ad, au, owner->num_sms, plan);
+    GroupCtl gch;
+    memset(&gch, 0, sizeof(gch));
+    gch.grid_d = plan.ctas_dots;
+    gch.grid_u = plan.ctas_upd;
+    RF_CUDA(cudaMemcpyAsync(bb + o_ad, ad.data(), sizeof(CocgArgs<T>) * cnt,
+                            cudaMemcpyHostToDevice, bs));
+    RF_CUDA(cudaMemcpyAsync(bb + o_au, au.data(), sizeof(CocgArgs<T>) * cnt,
+                            cudaMemcpyHostToDevice, bs));
+    RF_CUDA(cudaMemcpyAsync(bb + o_md, plan.map_dots.data(), sizeof(int) * plan.map_dots.size(),
+                            cudaMemcpyHostToDevice, bs));
+    RF_CUDA(cudaMemcpyAsync(bb + o_mu, plan.map_upd.data(), sizeof(int) * plan.map_upd.size(),
+                            cudaMemcpyHostToDevice, bs));
+    RF_CUDA(cudaMemcpyAsync(bb + o_gc, &gch, sizeof(gch), cudaMemcpyHostToDevice, bs));
+    RF_CUDA(cudaMemcpyAsync(bb + o_ggd, plan.gg_d.data(), sizeof(int) * plan.gg_d.size(),
+                            cudaMemcpyHostToDevice, bs));
+    RF_CUDA(cudaMemcpyAsync(bb + o_ggu, plan.gg_u.data(), sizeof(int) * plan.gg_u.size(),
+                            cudaMemcpyHostToDevice, bs));
+  };
+  std::vector<CocgCtl> ctl(cnt);
+  bool all_done = false;
+  std::vector<float> tk;  // dot ms, update ms per executed step (timed runs)
+  // capture `steps` steps of the current plan and replay the graph `reps`
+  // times (or until every problem is done); events bracket each kernel
+  auto run = [&](int steps, bool timed, int reps) {
+    std::vector<cudaEvent_t> evs;
+    if (timed) {
+      evs.resize(2 * steps + 1);
+      for (auto& e : evs) RF_CUDA(cudaEventCreate(&e));
+    }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    RF_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
+    try {
+      for (int it = 0; it < steps; ++it) {
+        if (timed) RF_CUDA(cudaEventRecordWithFlags(evs[2 * it], bs, cudaEventRecordExternal));
+        launch_ms_grouped<T>(plan, gd, 0, it & 1, bs);
+        if (timed)
+          RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], bs, cudaEventRecordExternal));
+        launch_ms_grouped<T>(plan, gd, 1, it & 1, bs);
+      }
+      if (timed) RF_CUDA(cudaEventRecordWithFlags(evs[2 * steps], bs, cudaEventRecordExternal));
+    } catch (...) {
+      g_capturing = false;
+      cudaStreamEndCapture(bs, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      for (auto& e : evs) cudaEventDestroy(e);
+      throw;
+    }
+    g_capturing = false;
+    RF_CUDA(cudaStreamEndCapture(bs, &graph));
+    RF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    RF_CUDA(cudaGraphDestroy(graph));
+    for (int r = 0; r < reps && !all_done; ++r) {
+      RF_CUDA(cudaGraphLaunch(exec, bs));
+      RF_CUDA(cudaMemcpyAsync(ctl.data(), ctl_d, sizeof(CocgCtl) * cnt, cudaMemcpyDeviceToHost,
+                              bs));
+      RF_CUDA(cudaStreamSynchronize(bs));
+      if (timed)
+        for (int k = 0; k < 2 * steps; ++k) {
+          float ms = 0.f;
+          RF_CUDA(cudaEventElapsedTime(&ms, evs[k], evs[k + 1]));
+          tk.push_back(ms);
+        }
+      owner->launches += 2 * steps;
+      owner->spmm_launches += 2 * steps;
+      all_done = true;
+      for (int t = 0; t < cnt; ++t) all_done = all_done && ctl[t].done;
+    }
+    RF_CUDA(cudaGraphExecDestroy(exec));
+    for (auto& e : evs) RF_CUDA(cudaEventDestroy(e));
+  };
+  // K10 autotuner for the batch: each candidate shape, applied to every
+  // problem, runs two real COCG steps of the batch; the fastest per kernel
+  // is kept on the first handle under the batch's signature `sig` (taken
+  // over all problems of the rafeast_solve_batched call, so the shapes tuned
+  // in the first outer iteration serve the later ones)
+  const bool prof = owner->opt_profile != 0;
+  Handle::Shape shp{0, 0, 0, 0};
+  bool have = false;
+  for (auto& kv : owner->tuned)
+    if (kv.first == sig) {
+      shp = kv.second;
+      have = true;
+    }
+  if (!have && owner->opt_autotune) {
+    const int cand[][2] = {{0, 0}, {32, 2}, {16, 2}, {16, 1}, {8, 2}, {8, 1},
+                           {16, 3}, {8, 3},  {16, 4}, {8, 4}};
+    const int capc = ms_max_cpl(fp64);
+    float best_d = 1e30f, best_u = 1e30f;
+    for (auto& c : cand) {
+      if (all_done) break;
+      if (c[1] > capc) continue;
+      auto v = shaped(c[0], c[1]);
+      prepare(v, v);
+      const size_t k0 = tk.size();
+      run(2, true, 1);
+      if (tk.size() < k0 + 4) break;
+      const float td = std::min(tk[k0], tk[k0 + 2]), tu = std::min(tk[k0 + 1], tk[k0 + 3]);
+      if (td < best_d) {
+        best_d = td;
+        shp.dl = c[0];
+        shp.dc = c[1];
+      }
+      if (tu < best_u) {
+        best_u = tu;
+        shp.ul = c[0];
+        shp.uc = c[1];
+      }
+    }
+    owner->tuned.push_back(std::make_pair(sig, shp));
   }
-  RF_CUDA(cudaGraphExecDestroy(exec));
-  for (auto& e : evs) RF_CUDA(cudaEventDestroy(e));
+  if (!all_done) {
+    prepare(shaped(shp.dl, shp.dc), shaped(shp.ul, shp.uc));
+    int chunk = std::max(2, owner->opt_chunk);
+    chunk += chunk & 1;
+    int max_inner = 1;
+    for (auto* it : items) max_inner = std::max(max_inner, it->prm->max_inner);
+    run(chunk, prof, (max_inner + 2) / chunk + 2);
+  }
+  owner->prof[6] = shp.dl * 100 + shp.dc;
+  owner->prof[7] = shp.ul * 100 + shp.uc;
   if (prof && all_done) {
     // per-step time of the grouped kernels against the algorithmic bytes of
     // every problem still active in that step
@@ -950,8 +1025,6 @@ static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cud
         owner->prof[5] += bu;
       }
     }
-    owner->prof[6] = 0;
-    owner->prof[7] = 0;
   }
   for (int t = 0; t < cnt; ++t) {
     Handle* h = items[t]->h;
@@ -1995,6 +2068,11 @@ int rafeast_solve_batched(int count, rafeast_t const* hs, const rafeast_params* 
     owner->last_rhist.clear();
     owner->last_tk.clear();
   }
+  // signature of the batch for the shape autotuner (negative: batch keys)
+  int64_t sig = count;
+  for (int t = 0; t < count; ++t)
+    sig = sig * 1000003 + H[t]->n * 131 + prms[t].m0 * 7 + prms[t].nc;
+  sig = -(sig & 0x3fffffffffffffffLL) - 1;
   std::vector<char> done(count, 0);
   int max_outer = 0;
   for (int t = 0; t < count; ++t) max_outer = std::max(max_outer, prms[t].max_outer);
@@ -2009,8 +2087,8 @@ int rafeast_solve_batched(int count, rafeast_t const* hs, const rafeast_params* 
         RF_CUDA(cudaEventRecord(runs[t].ev[2], bs));
       }
     if (act.empty()) break;
-    if (prms[0].precision == RAFEAST_FP64) filter_ms_batched<double>(act_items, owner, bs);
-    else filter_ms_batched<float>(act_items, owner, bs);
+    if (prms[0].precision == RAFEAST_FP64) filter_ms_batched<double>(act_items, owner, bs, sig);
+    else filter_ms_batched<float>(act_items, owner, bs, sig);
     for (int t : act) {
       runs[t].fs = items[t].fs;
       runs[t].cocg_total += items[t].fs.iters_max;

@@ -251,24 +251,28 @@ struct GroupCtl {
 struct GroupPlan {
   int count = 0;
   int ns = 0;
-  int mc = 2;  // compiled chunks per lane of both kernels
+  int mc_d = 2, mc_u = 2;  // compiled chunks per lane of the two kernels
   size_t smem_dots = 0, smem_upd = 0;
   const void* fn_dots = nullptr;
   const void* fn_upd = nullptr;
   std::vector<int> map_dots, map_upd;  // initial maps (every problem active)
-  std::vector<int> gg;  // per problem: row groups, column blocks, gathered KiB, 0
+  std::vector<int> gg_d, gg_u;  // per problem: row groups, column blocks, gathered KiB, 0
   int ctas_dots = 0, ctas_upd = 0;  // persistent grid sizes
 };
+// the two kernels may use different (lanes, chunks) shapes per problem
 template <typename T> struct GroupDev {
-  const CocgArgs<T>* args;
+  const CocgArgs<T>* args_d;
+  const CocgArgs<T>* args_u;
   int* map_d;
   int* map_u;
   GroupCtl* gc;
   const CocgCtl* ctl;  // the problems' control blocks, contiguous
-  const int4* gg;
+  const int4* gg_d;
+  const int4* gg_u;
 };
 template <typename T>
-void plan_ms_grouped(const std::vector<CocgArgs<T>>& args, int num_sms, GroupPlan& g);
+void plan_ms_grouped(const std::vector<CocgArgs<T>>& args_d, const std::vector<CocgArgs<T>>& args_u,
+                     int num_sms, GroupPlan& g);
 // which: 0 dots (seed scalars of every problem, then the re-plan), 1 update
 template <typename T>
 void launch_ms_grouped(const GroupPlan& g, const GroupDev<T>& d, int which, int buf,

@@ -59,39 +59,43 @@ __device__ __forceinline__ int block_scan(int v, int* total) {
 // mult x grid items, mult = max(ITEMS_PER_CTA, gathered state / WINDOW_KB),
 // i.e. the items in flight at any time share about WINDOW_KB of gathered
 // state. map[0..count] item starts, map[count + 1 + t] = gx_t (>= 1).
-__device__ void plan_items(const CocgCtl* __restrict__ ctl, const int4* __restrict__ gg,
-                           int count, int grid_d, int grid_u, int* __restrict__ map_d,
-                           int* __restrict__ map_u) {
-  __shared__ long long s_red[2][WARPS];
+__device__ void plan_items(const CocgCtl* __restrict__ ctl, const int4* __restrict__ gg_d,
+                           const int4* __restrict__ gg_u, int count, int grid_d, int grid_u,
+                           int* __restrict__ map_d, int* __restrict__ map_u) {
+  __shared__ long long s_red[3][WARPS];
   __shared__ long long s_R[2];
-  long long work = 0, wkb = 0;
+  long long work_d = 0, work_u = 0, wkb = 0;
   for (int t = threadIdx.x; t < count; t += blockDim.x)
     if (!__ldcg(&ctl[t].done)) {
-      const int4 g = gg[t];
-      work += (long long)g.x * g.y;
+      const int4 g = gg_d[t], h = gg_u[t];
+      work_d += (long long)g.x * g.y;
+      work_u += (long long)h.x * h.y;
       wkb += g.z;
     }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    work += __shfl_xor_sync(0xffffffffu, work, o);
+    work_d += __shfl_xor_sync(0xffffffffu, work_d, o);
+    work_u += __shfl_xor_sync(0xffffffffu, work_u, o);
     wkb += __shfl_xor_sync(0xffffffffu, wkb, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    s_red[0][threadIdx.x >> 5] = work;
-    s_red[1][threadIdx.x >> 5] = wkb;
+    s_red[0][threadIdx.x >> 5] = work_d;
+    s_red[1][threadIdx.x >> 5] = work_u;
+    s_red[2][threadIdx.x >> 5] = wkb;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    long long W = 0, K = 0;
+    long long Wd = 0, Wu = 0, K = 0;
     for (int w = 0; w < WARPS; ++w) {
-      W += s_red[0][w];
-      K += s_red[1][w];
+      Wd += s_red[0][w];
+      Wu += s_red[1][w];
+      K += s_red[2][w];
     }
     long long mult = (K + WINDOW_KB - 1) / WINDOW_KB;
     if (mult < ITEMS_PER_CTA) mult = ITEMS_PER_CTA;
     const long long td = mult * grid_d, tu = mult * grid_u;
-    s_R[0] = W > td ? (W + td - 1) / td : 1;
-    s_R[1] = W > tu ? (W + tu - 1) / tu : 1;
+    s_R[0] = Wd > td ? (Wd + td - 1) / td : 1;
+    s_R[1] = Wu > tu ? (Wu + tu - 1) / tu : 1;
   }
   __syncthreads();
   const long long Rd = s_R[0], Ru = s_R[1];
@@ -100,15 +104,15 @@ __device__ void plan_items(const CocgCtl* __restrict__ ctl, const int4* __restri
     const int t = base + threadIdx.x;
     int nd = 0, nu = 0, gxd = 1, gxu = 1;
     if (t < count && !__ldcg(&ctl[t].done)) {
-      const int4 g = gg[t];
+      const int4 g = gg_d[t], h = gg_u[t];
       gxd = (int)((g.x + Rd - 1) / Rd);
-      gxu = (int)((g.x + Ru - 1) / Ru);
+      gxu = (int)((h.x + Ru - 1) / Ru);
       if (gxd < 1) gxd = 1;
       if (gxu < 1) gxu = 1;
       nd = gxd * g.y;
-      nu = gxu * g.y;
+      nu = gxu * h.y;
     }
-    int tot_d = 0, tot_u = 0;
+  int tot_d = 0, tot_u = 0;
     const int pd = block_scan(nd, &tot_d);
     const int pu = block_scan(nu, &tot_u);
     if (t < count) {
@@ -180,8 +184,8 @@ template <typename T, int MAXCPL>
 __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && MAXCPL * 2 <= 4) ? 2 : 1)
     k_ms_dots_grouped(const CocgArgs<T>* __restrict__ args, int* __restrict__ map_d,
                       int* __restrict__ map_u, GroupCtl* __restrict__ gc,
-                      const CocgCtl* __restrict__ ctl, const int4* __restrict__ gg, int count,
-                      int buf) {
+                      const CocgCtl* __restrict__ ctl, const int4* __restrict__ gg_d,
+                      const int4* __restrict__ gg_u, int count, int buf) {
   __shared__ int smap[2 * SMEM_MAP + 1];
   __shared__ int s_glast;
   const MapView m = stage_map(map_d, count, smap);
@@ -203,7 +207,7 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && MAXCPL * 2 <= 4) ?
   __syncthreads();
   if (s_glast) {
     __threadfence();
-    plan_items(ctl, gg, count, gc->grid_d, gc->grid_u, map_d, map_u);
+    plan_items(ctl, gg_d, gg_u, count, gc->grid_d, gc->grid_u, map_d, map_u);
     if (threadIdx.x == 0) {
       gc->next_d = 0;
       gc->next_u = 0;
@@ -267,13 +271,10 @@ static const void* upd_fn(int mc, int ns) {
 }
 
 // initial item maps (every problem active), same rule as the device planner
-static void plan_host(const std::vector<int>& gg, int grid, std::vector<int>& map) {
+static void plan_host(const std::vector<int>& gg, long long wkb, int grid, std::vector<int>& map) {
   const int cnt = (int)gg.size() / 4;
-  long long work = 0, wkb = 0;
-  for (int t = 0; t < cnt; ++t) {
-    work += (long long)gg[4 * t] * gg[4 * t + 1];
-    wkb += gg[4 * t + 2];
-  }
+  long long work = 0;
+  for (int t = 0; t < cnt; ++t) work += (long long)gg[4 * t] * gg[4 * t + 1];
   long long mult = std::max<long long>(ITEMS_PER_CTA, (wkb + WINDOW_KB - 1) / WINDOW_KB);
   const long long target = mult * grid;
   const long long R = work > target ? (work + target - 1) / target : 1;
@@ -290,62 +291,81 @@ static void plan_host(const std::vector<int>& gg, int grid, std::vector<int>& ma
   map[cnt] = (int)start;
 }
 
+// per problem: row groups, column blocks, gathered state (KiB), 0
 template <typename T>
-void plan_ms_grouped(const std::vector<CocgArgs<T>>& args, int num_sms, GroupPlan& g) {
+static void shapes_of(const std::vector<CocgArgs<T>>& args, std::vector<int>& gg) {
   const int cnt = (int)args.size();
-  RF_CHECK(cnt >= 1, RAFEAST_ERR_INVALID_ARG);
-  g.count = cnt;
-  g.ns = args[0].ns;
-  int maxcpl = 1, maxlanes = 4, maxlc = 1;
-  for (const auto& a : args) {
-    RF_CHECK(a.ns == g.ns && a.ms == 1, RAFEAST_ERR_INVALID_ARG);
-    RF_CHECK(a.cpl >= 1 && a.cpl <= grouped_mc_large<T>(), RAFEAST_ERR_INVALID_ARG);
-    maxcpl = std::max(maxcpl, a.cpl);
-    maxlanes = std::max(maxlanes, a.lanes);
-    maxlc = std::max(maxlc, a.lanes * a.cpl);
-  }
-  g.mc = maxcpl <= 2 ? 2 : grouped_mc_large<T>();
-  g.smem_dots = (size_t)maxlanes * g.mc * 2 * 5 * sizeof(double);
-  g.smem_upd = (size_t)2 * maxlc * (sizeof(Coef<T>) + g.ns * sizeof(ShiftCoef<T>)) + 16;
-  g.fn_dots = dots_fn<T>(g.mc);
-  g.fn_upd = upd_fn<T>(g.mc, g.ns);
-  if (g.smem_upd > 48 * 1024) ensure_dyn_smem(g.fn_upd, g.smem_upd);
-  int occ_d = 0, occ_u = 0;
-  RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, g.fn_dots, THREADS, g.smem_dots));
-  RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, g.fn_upd, THREADS, g.smem_upd));
-  g.gg.assign(4 * cnt, 0);
+  gg.assign(4 * cnt, 0);
   for (int t = 0; t < cnt; ++t) {
     const auto& a = args[t];
     const int64_t per = (int64_t)WARPS * (32 / a.lanes);
     const int64_t groups = (a.n + per - 1) / per;
     RF_CHECK(groups < 0x7fffffff, RAFEAST_ERR_INVALID_ARG);
-    g.gg[4 * t] = (int)groups;
-    g.gg[4 * t + 1] = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);
-    // gathered state: seed r and p of every pair, KiB
-    g.gg[4 * t + 2] = (int)std::min<int64_t>(
+    gg[4 * t] = (int)groups;
+    gg[4 * t + 1] = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);
+    // seed r and p of every pair
+    gg[4 * t + 2] = (int)std::min<int64_t>(
         0x7fffffff, (a.n * (int64_t)a.m0 * 2 * 2 * 2 * (int64_t)sizeof(T) + 1023) / 1024);
   }
+}
+
+template <typename T>
+void plan_ms_grouped(const std::vector<CocgArgs<T>>& args_d, const std::vector<CocgArgs<T>>& args_u,
+                     int num_sms, GroupPlan& g) {
+  const int cnt = (int)args_d.size();
+  RF_CHECK(cnt >= 1 && (int)args_u.size() == cnt, RAFEAST_ERR_INVALID_ARG);
+  g.count = cnt;
+  g.ns = args_d[0].ns;
+  int cd = 1, cu = 1, ld = 4, lcu = 1;
+  for (int t = 0; t < cnt; ++t) {
+    const auto& a = args_d[t];
+    const auto& b = args_u[t];
+    RF_CHECK(a.ns == g.ns && b.ns == g.ns && a.ms == 1 && b.ms == 1, RAFEAST_ERR_INVALID_ARG);
+    RF_CHECK(a.cpl >= 1 && a.cpl <= grouped_mc_large<T>() && b.cpl >= 1 &&
+                 b.cpl <= grouped_mc_large<T>(),
+             RAFEAST_ERR_INVALID_ARG);
+    cd = std::max(cd, a.cpl);
+    cu = std::max(cu, b.cpl);
+    ld = std::max(ld, a.lanes);
+    lcu = std::max(lcu, b.lanes * b.cpl);
+  }
+  g.mc_d = cd <= 2 ? 2 : grouped_mc_large<T>();
+  g.mc_u = cu <= 2 ? 2 : grouped_mc_large<T>();
+  g.smem_dots = (size_t)ld * g.mc_d * 2 * 5 * sizeof(double);
+  g.smem_upd = (size_t)2 * lcu * (sizeof(Coef<T>) + g.ns * sizeof(ShiftCoef<T>)) + 16;
+  g.fn_dots = dots_fn<T>(g.mc_d);
+  g.fn_upd = upd_fn<T>(g.mc_u, g.ns);
+  if (g.smem_upd > 48 * 1024) ensure_dyn_smem(g.fn_upd, g.smem_upd);
+  int occ_d = 0, occ_u = 0;
+  RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, g.fn_dots, THREADS, g.smem_dots));
+  RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, g.fn_upd, THREADS, g.smem_upd));
+  shapes_of(args_d, g.gg_d);
+  shapes_of(args_u, g.gg_u);
+  long long wkb = 0;
+  for (int t = 0; t < cnt; ++t) wkb += g.gg_d[4 * t + 2];
   g.ctas_dots = num_sms * std::max(occ_d, 1);
   g.ctas_upd = num_sms * std::max(occ_u, 1);
-  plan_host(g.gg, g.ctas_dots, g.map_dots);
-  plan_host(g.gg, g.ctas_upd, g.map_upd);
+  plan_host(g.gg_d, wkb, g.ctas_dots, g.map_dots);
+  plan_host(g.gg_u, wkb, g.ctas_upd, g.map_upd);
 }
 
 template <typename T>
 void launch_ms_grouped(const GroupPlan& g, const GroupDev<T>& d, int which, int buf,
                        cudaStream_t s) {
   int cnt = g.count;
-  const CocgArgs<T>* ap = d.args;
   GroupCtl* gc = d.gc;
   if (which == 0) {
+    const CocgArgs<T>* ap = d.args_d;
     int* md = d.map_d;
     int* mu = d.map_u;
     const CocgCtl* ctl = d.ctl;
-    const int4* gg = d.gg;
-    void* params[] = {(void*)&ap, (void*)&md, (void*)&mu, (void*)&gc, (void*)&ctl, (void*)&gg,
-                      (void*)&cnt, (void*)&buf};
+    const int4* ggd = d.gg_d;
+    const int4* ggu = d.gg_u;
+    void* params[] = {(void*)&ap,  (void*)&md,  (void*)&mu,  (void*)&gc, (void*)&ctl,
+                      (void*)&ggd, (void*)&ggu, (void*)&cnt, (void*)&buf};
     RF_CUDA(cudaLaunchKernel(g.fn_dots, dim3(g.ctas_dots), dim3(THREADS), params, g.smem_dots, s));
   } else {
+    const CocgArgs<T>* ap = d.args_u;
     const int* mu = d.map_u;
     void* params[] = {(void*)&ap, (void*)&mu, (void*)&gc, (void*)&cnt, (void*)&buf};
     RF_CUDA(cudaLaunchKernel(g.fn_upd, dim3(g.ctas_upd), dim3(THREADS), params, g.smem_upd, s));
@@ -353,8 +373,10 @@ void launch_ms_grouped(const GroupPlan& g, const GroupDev<T>& d, int which, int 
   RF_LAUNCH();
 }
 
-template void plan_ms_grouped<float>(const std::vector<CocgArgs<float>>&, int, GroupPlan&);
-template void plan_ms_grouped<double>(const std::vector<CocgArgs<double>>&, int, GroupPlan&);
+template void plan_ms_grouped<float>(const std::vector<CocgArgs<float>>&,
+                                     const std::vector<CocgArgs<float>>&, int, GroupPlan&);
+template void plan_ms_grouped<double>(const std::vector<CocgArgs<double>>&,
+                                      const std::vector<CocgArgs<double>>&, int, GroupPlan&);
 template void launch_ms_grouped<float>(const GroupPlan&, const GroupDev<float>&, int, int,
                                        cudaStream_t);
 template void launch_ms_grouped<double>(const GroupPlan&, const GroupDev<double>&, int, int,
