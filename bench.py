@@ -66,6 +66,23 @@ def _traffic_per_launch(kernel: str, workload: str):
     return None
 
 
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest `value` over all ranks (time-like quantities of a replica
+    run: the whole job ends with its slowest rank); identity without a
+    process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units of all replicas per second over the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -163,6 +180,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     key = WORKLOADS[args.workload]["key"]
+    if key == "sbm64":
+        return _run_reference_sbm(args)
     counts = _reference_counts(key)
     samples = []
     for i in range(args.warmup + args.steps):
@@ -185,6 +204,39 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _run_reference_sbm(args):
+    """--impl reference --workload sbm64: the oracle on the median instance,
+    scaled by nnz to all 64 and to the GPU solve's mean iteration counts."""
+    from types import SimpleNamespace
+    from workloads import configs as CF
+    insts = CF.sbm_instances()
+    gold = CF.load_golden()["sbm64"]["instances"]
+    # mean per-instance counts of the batched GPU solve (22.4 outer iterations,
+    # 38,100 COCG steps over the 64 instances)
+    infos = [SimpleNamespace(outer_iters=22, cocg_iters_total=595) for _ in insts]
+    ests = []
+    for i in range(args.warmup + args.steps):
+        d = _cpu_sample_sbm(insts, gold, infos)
+        if "error" in d:
+            print(json.dumps({"impl": "reference", "unavailable": d["error"][-200:]}))
+            return 0
+        if i >= args.warmup:
+            ests.append(d)
+    est = statistics.mean(d["est"] for d in ests)
+    value = len(insts) / est
+    line = {"metric": METRIC, "value": value, "unit": "problems/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sbm64: 64 stochastic-block-model Laplacians, batched"},
+            "cpu_baseline": {"value": value, "unit": "problems/s", "cores": 1, "kind": "oracle",
+                             "sample": ests[0]["sample"]},
+            "e2e": {"value": value, "unit": "problems/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -290,10 +342,7 @@ def run_batched(args):
     ms = e0.elapsed_time(e1)
     prof = R.rafeast_profile(hs[0], reset=True)
     R.rafeast_set_option(hs[0], R.RAFEAST_OPT_PROFILE, 0)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
     # parity: every instance's eigenvalues against its stored Lanczos spectrum
     worst, found_all = 0.0, True
@@ -351,7 +400,7 @@ def run_batched(args):
                                  "ms_per_launch": prof[f"{other}_ms"] / max(prof[f"{other}_launches"], 1)},
                 "share_of_step": (prof["update_ms"] + prof["dots_ms"]) / ms}
     ns = [lap.n for lap in laps]
-    value = args.steps * cnt * world / (ms / 1e3)
+    value = whole_job_rate(args.steps * cnt, world, ms)
     line = {"metric": METRIC, "value": value, "unit": "problems/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "time_to_solution_s": ms_step / 1e3, "higher_is_better": True, "scaling": "weak",
@@ -415,10 +464,7 @@ def run_batched(args):
         e2e_step()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, dist, dev)
         line["e2e"] = {"value": cnt * world / el, "unit": "problems/s",
                        "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": 1,
                        "includes": "rafeast_create of all 64 from pinned host CSR, warmstarts, "
@@ -575,13 +621,9 @@ def main():
     ms = e0.elapsed_time(e1)
     prof = R.rafeast_profile(h, reset=True)
     R.rafeast_set_option(h, R.RAFEAST_OPT_PROFILE, 0)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
-    total_solves = args.steps * world
-    value = total_solves / (ms / 1e3)
+    value = whole_job_rate(args.steps, world, ms)
     # parity of the last timed step against the stored ARPACK eigenvalues
     mf, info = infos[-1]
     ev = evals.cpu().numpy()[:mf]
@@ -675,10 +717,7 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, dist, dev)
         line["e2e"] = {"value": ek * world / el, "unit": "solves/s", "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo, "steps": ek,
                        "includes": "rafeast_create from pinned host CSR (row reorder on the "

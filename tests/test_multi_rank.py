@@ -1,0 +1,62 @@
+"""The N > 1 path of bench.py on CPU: one replica per rank (the path has no
+exchange step), max-over-ranks timing and the whole-job rate, on a
+world-size-2 gloo process group; the reference arm's rank 1 exits without
+work or output."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # ranks finish their timed steps at different times; everyone must see
+    # the slowest one
+    ms = [1200.0, 1500.0][rank]
+    mx = bench.max_over_ranks(ms, dist)
+    rate = bench.whole_job_rate(3, world, mx)
+    with open(os.path.join(out, f"r{rank}.json"), "w") as f:
+        json.dump({"max": mx, "rate": rate}, f)
+    dist.destroy_process_group()
+
+
+def test_replica_timing_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_rank, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn")
+    res = [json.load(open(tmp_path / f"r{r}.json")) for r in range(2)]
+    assert res[0]["max"] == res[1]["max"] == 1500.0
+    # 3 units per rank, 2 ranks, over the slowest rank's 1.5 s
+    assert res[0]["rate"] == pytest.approx(4.0)
+
+
+def test_single_rank_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(12.5) == 12.5
+    assert bench.whole_job_rate(2, 1, 500.0) == pytest.approx(4.0)
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "0"],
+                       capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
