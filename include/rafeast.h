@@ -175,8 +175,10 @@ int rafeast_set_option(rafeast_t h, int key, int64_t value);
  * launched while RAFEAST_OPT_PROFILE was on (CUDA events recorded around each
  * kernel inside the replayed graphs). out (host, 8 doubles): dot-kernel
  * launches, milliseconds, bytes; update-kernel launches, milliseconds, bytes;
- * the kernel shapes of the last multi-shift solve as 100*lanes + chunks per
- * lane (dot kernel, update kernel; chosen by the autotuner). Bytes count A once (nnz*(4+s) + 4(n+1), s = 4 or 8) plus each state
+ * the kernel shapes of the last multi-shift solve as 10000*c + 100*lanes +
+ * chunks per lane, c the CTAs per SM the chosen kernel instance is compiled
+ * for (0: the default instance; dot kernel, update kernel; chosen by the
+ * autotuner). Bytes count A once (nnz*(4+s) + 4(n+1), s = 4 or 8) plus each state
  * column the launch reads or writes once: the dot kernel reads r, the update
  * kernel reads r and p, writes r and p, and updates the quadrature sum. With
  * reset != 0 the counters restart at zero after being copied out. */

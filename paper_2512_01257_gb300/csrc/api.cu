@@ -686,6 +686,7 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
   // event nodes) at the start of this solve; the fastest per kernel is kept
   // for this handle. Shapes change only the work split, not the arithmetic.
   CocgArgs<T> ad = a, au = a;
+  ad.occ = au.occ = 0;
   const int64_t key = ((int64_t)pairs << 20) | ((int64_t)ns << 4) | (fp64 ? 1 : 0);
   const int cap = h->opt_cpl > 0 ? std::min(h->opt_cpl, ms_max_cpl(fp64)) : ms_max_cpl(fp64);
   bool have = false;
@@ -693,22 +694,29 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
     if (kv.first == key) {
       ad.lanes = kv.second.dl;
       ad.cpl = kv.second.dc;
+      ad.occ = kv.second.dm;
       au.lanes = kv.second.ul;
       au.cpl = kv.second.uc;
+      au.occ = kv.second.um;
       have = true;
     }
   if (!have && h->opt_autotune && !h->opt_lanes && !h->opt_cpl) {
-    const int cand[][2] = {{32, 2}, {16, 2}, {16, 3}, {16, 4}, {8, 1}, {8, 2}, {8, 4}, {4, 2}};
+    // (lanes, chunks, CTAs per SM; 0 = the default instance)
+    const int cand[][3] = {{32, 2, 0}, {16, 2, 0}, {16, 3, 0}, {16, 4, 0}, {8, 1, 0},
+                           {8, 2, 0},  {8, 4, 0},  {4, 2, 0},  {32, 2, 3}, {16, 2, 3},
+                           {8, 2, 3},  {16, 2, 4}};
     float best_d = 1e30f, best_u = 1e30f;
     for (auto& c : cand) {
       if (ctl.done) break;
       const int G = c[0], cpl = c[1];
       if (cpl > cap) continue;
+      if (c[2] && fp64) continue;
       const int blocks = (pairs + G * cpl - 1) / (G * cpl);
       if ((double)pairs / (blocks * G * cpl) < 0.5) continue;
       CocgArgs<T> t = a;
       t.lanes = G;
       t.cpl = cpl;
+      t.occ = c[2];
       std::vector<cudaEvent_t> evs;
       cudaGraphExec_t exec = nullptr;
       capture(t, t, 2, true, evs, exec);
@@ -724,22 +732,26 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
         best_d = td;
         ad.lanes = G;
         ad.cpl = cpl;
+        ad.occ = c[2];
       }
       if (tu < best_u) {
         best_u = tu;
         au.lanes = G;
         au.cpl = cpl;
+        au.occ = c[2];
       }
     }
     Handle::Shape shp;
     shp.dl = ad.lanes;
     shp.dc = ad.cpl;
+    shp.dm = ad.occ;
     shp.ul = au.lanes;
     shp.uc = au.cpl;
+    shp.um = au.occ;
     h->tuned.push_back(std::make_pair(key, shp));
   }
-  h->prof[6] = ad.lanes * 100 + ad.cpl;
-  h->prof[7] = au.lanes * 100 + au.cpl;
+  h->prof[6] = ad.occ * 10000 + ad.lanes * 100 + ad.cpl;
+  h->prof[7] = au.occ * 10000 + au.lanes * 100 + au.cpl;
   int chunk = std::max(2, h->opt_chunk);
   chunk += chunk & 1;
   std::vector<cudaEvent_t> evs;

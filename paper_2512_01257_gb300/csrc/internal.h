@@ -127,6 +127,10 @@ template <typename T> struct CocgArgs {
   ShiftCoef<T>* scf;       // [columns * ns]
   T* ps;                   // shifted directions, row r: pairs x ns x 2 complex
   int ldps;                // complex stride of a ps row
+  // resident CTAs per SM the multi-shift kernels are compiled for (float,
+  // at most two chunks per lane): 0 or 2 the default instances, 3 or 4
+  // instances with fewer registers per thread (host-side choice)
+  int occ;
 };
 
 // ---- handle -----------------------------------------------------------------
@@ -169,6 +173,7 @@ struct Handle {
   // kernels, keyed by (pairs, shifts, precision)
   struct Shape {
     int dl, dc, ul, uc;
+    int dm = 0, um = 0;  // forced CTAs per SM (0: default instance)
   };
   std::vector<std::pair<int64_t, Shape>> tuned;
   int opt_profile = 0;
