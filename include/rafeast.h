@@ -97,6 +97,13 @@ extern "C" {
                                      * per column, other shifts from its       *
                                      * scalars; same iterates in exact         *
                                      * arithmetic)                              */
+#define RAFEAST_OPT_UPDATE 12       /* multi-shift update kernel: 0 auto    *
+                                     * (streamed), 1 gathered products (M p_k *
+                                     * recomputed from gathered r and p), 2   *
+                                     * streamed (the dot kernel stores M r_k, *
+                                     * M p_k follows by its recurrence; no    *
+                                     * gathers in the update). Batched solves *
+                                     * use the gathered form.                 */
 #define RAFEAST_OPT_TEST_STALL 9    /* test hook: bytes (multiple of 16) that  *
                                      * every bulk-copy stage waits for and no *
                                      * copy delivers, so the bounded wait     *

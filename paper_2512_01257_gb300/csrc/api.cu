@@ -457,7 +457,7 @@ template <typename T>
 static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double* Qd,
                              const double* AQd, const double* theta_d,
                              const std::vector<double>& theta, int m0, int ldq, CocgCtl* ctl_dev,
-                             bool profile, cudaStream_t st) {
+                             bool profile, bool stream, cudaStream_t st) {
   using C = c2<T>;
   const int nc = prm.nc;
   const bool fp64 = sizeof(T) == 8;
@@ -544,10 +544,18 @@ static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double*
   int colblocks = 1;
   choose_shape(pairs, 2, fp64, h->opt_lanes, a.lanes, a.cpl, colblocks,
                h->opt_cpl > 0 ? std::min(h->opt_cpl, ms_max_cpl(fp64)) : ms_max_cpl(fp64));
-  a.r[0] = state;
-  a.r[1] = state + seed_elems;
-  a.p[0] = state + 2 * seed_elems;
-  a.p[1] = state + 3 * seed_elems;
+  if (stream) {
+    // r and p in place, w = M r and s = M p beside them
+    a.r[0] = a.r[1] = state;
+    a.p[0] = a.p[1] = state + seed_elems;
+    a.wbuf = state + 2 * seed_elems;
+    a.sbuf = state + 3 * seed_elems;
+  } else {
+    a.r[0] = state;
+    a.r[1] = state + seed_elems;
+    a.p[0] = state + 2 * seed_elems;
+    a.p[1] = state + 3 * seed_elems;
+  }
   a.ps = state + 4 * seed_elems;
   a.ldps = ldps;
   a.dacc = dacc;
@@ -593,17 +601,22 @@ static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double*
 // active in the dot kernel and act_u in the update kernel: A once per kernel;
 // the dot kernel reads the seed residual; the update kernel reads and writes
 // the seed r and p, the shifted directions and the quadrature sum
-static double ms_dots_bytes(const Handle* h, int act_d, bool fp64) {
+// (streamed update: the dot kernel also writes w; the update kernel reads
+// r, p, w, s and writes r, p, s, and reads no A)
+static double ms_dots_bytes(const Handle* h, int act_d, bool fp64, bool stream = false) {
   const double sv = fp64 ? 8.0 : 4.0;
   const double abytes = (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
   const double pairb = (double)h->n * 2 * 2.0 * sv;
-  return abytes + pairb * act_d;
+  return abytes + pairb * act_d * (stream ? 2.0 : 1.0);
 }
-static double ms_update_bytes(const Handle* h, int act_u, int ns, bool fp64) {
+static double ms_update_bytes(const Handle* h, int act_u, int ns, bool fp64,
+                              bool stream = false) {
   const double sv = fp64 ? 8.0 : 4.0;
   const double abytes = (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
   const double pairb = (double)h->n * 2 * 2.0 * sv;
-  return abytes + (4.0 + 2.0 * ns) * pairb * act_u + 2.0 * (double)h->n * 2 * act_u * sv;
+  const double dacc = 2.0 * (double)h->n * 2 * act_u * sv;
+  if (stream) return (7.0 + 2.0 * ns) * pairb * act_u + dacc;
+  return abytes + (4.0 + 2.0 * ns) * pairb * act_u + dacc;
 }
 
 // combine Qt = f Q + D and the solve's statistics (after the device reported done)
@@ -626,8 +639,9 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
                           const std::vector<double>& theta, int m0, int ldq, double* Qt,
                           FilterStats& fs) {
   const bool fp64 = sizeof(T) == 8;
+  const bool stream = h->opt_update != 1;
   MsProblem<T> P = ms_setup<T>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, nullptr,
-                                h->opt_profile != 0, h->stream);
+                                h->opt_profile != 0, stream, h->stream);
   const CocgArgs<T>& a = P.a;
   const int pairs = P.pairs, ns = P.ns;
   const bool prof = h->opt_profile != 0;
@@ -652,7 +666,8 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
         launch_cocg_dots<T>(ad, 2, it & 1, h->num_sms, h->stream);
         if (timed)
           RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], h->stream, cudaEventRecordExternal));
-        launch_ms_update<T>(au, it & 1, h->num_sms, h->stream);
+        if (stream) launch_ms_update_stream<T>(au, h->num_sms, h->stream);
+        else launch_ms_update<T>(au, it & 1, h->num_sms, h->stream);
       }
       if (timed)
         RF_CUDA(cudaEventRecordWithFlags(evs[2 * steps], h->stream, cudaEventRecordExternal));
@@ -687,7 +702,8 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
   // for this handle. Shapes change only the work split, not the arithmetic.
   CocgArgs<T> ad = a, au = a;
   ad.occ = au.occ = 0;
-  const int64_t key = ((int64_t)pairs << 20) | ((int64_t)ns << 4) | (fp64 ? 1 : 0);
+  const int64_t key =
+      ((int64_t)pairs << 20) | ((int64_t)ns << 4) | (stream ? 2 : 0) | (fp64 ? 1 : 0);
   const int cap = h->opt_cpl > 0 ? std::min(h->opt_cpl, ms_max_cpl(fp64)) : ms_max_cpl(fp64);
   bool have = false;
   for (auto& kv : h->tuned)
@@ -778,11 +794,11 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
       const int act_u = hist[k];
       h->prof[0] += 1;
       h->prof[1] += tk[2 * k];
-      h->prof[2] += ms_dots_bytes(h, act_d, fp64);
+      h->prof[2] += ms_dots_bytes(h, act_d, fp64, stream);
       if (act_u > 0) {
         h->prof[3] += 1;
         h->prof[4] += tk[2 * k + 1];
-        h->prof[5] += ms_update_bytes(h, act_u, ns, fp64);
+        h->prof[5] += ms_update_bytes(h, act_u, ns, fp64, stream);
       }
     }
   }
@@ -840,7 +856,7 @@ static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cud
   for (int t = 0; t < cnt; ++t) {
     Handle* h = items[t]->h;
     P[t] = ms_setup<T>(h, *items[t]->prm, h->Q, h->AQ, h->theta_d, h->theta, h->m0, h->ldq,
-                       ctl_d + t, owner->opt_profile != 0, bs);
+                       ctl_d + t, owner->opt_profile != 0, false, bs);
   }
   GroupDev<T> gd;
   gd.args_d = (const CocgArgs<T>*)(bb + o_ad);
@@ -1553,6 +1569,10 @@ int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
     case RAFEAST_OPT_SOLVER:
       if (value < 0 || value > 1) return RAFEAST_ERR_INVALID_ARG;
       h->opt_solver = (int)value;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_UPDATE:
+      if (value < 0 || value > 2) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_update = (int)value;
       return RAFEAST_OK;
     case RAFEAST_OPT_CPL:
       if (value < 0 || value > 16) return RAFEAST_ERR_INVALID_ARG;

@@ -206,11 +206,12 @@ __device__ __forceinline__ void cocg_dots_body(const CocgArgs<T>& a, const CocgA
 #pragma unroll
       for (int c = 0; c < MAXCPL; ++c)
         if (mask & (1u << c)) {
-          C rv[NC];
+          C rv[NC], wv[NC];
           ld_chunk<NC>(R + row * ldt + coff[c], rv);
 #pragma unroll
           for (int j = 0; j < NC; ++j) {
             const C w = csub<T>(cmul<T>(zv[j], rv[j]), acc[c][j]);
+            wv[j] = w;
             // gamma += r r, delta += r w, nu += |r|^2
             dg_re[c][j] = fma(rv[j].x, rv[j].x, fma(-rv[j].y, rv[j].y, dg_re[c][j]));
             dg_im[c][j] = fma((T)2 * rv[j].x, rv[j].y, dg_im[c][j]);
@@ -218,6 +219,8 @@ __device__ __forceinline__ void cocg_dots_body(const CocgArgs<T>& a, const CocgA
             dd_im[c][j] = fma(rv[j].x, w.y, fma(rv[j].y, w.x, dd_im[c][j]));
             dn[c][j] = fma(rv[j].x, rv[j].x, fma(rv[j].y, rv[j].y, dn[c][j]));
           }
+          // streamed update: keep w = M r for the update kernel
+          if (a.wbuf) st_chunk<NC>(a.wbuf + row * ldt + coff[c], wv);
         }
     }
   }

@@ -131,6 +131,12 @@ template <typename T> struct CocgArgs {
   // at most two chunks per lane): 0 or 2 the default instances, 3 or 4
   // instances with fewer registers per thread (host-side choice)
   int occ;
+  // streamed multi-shift update (wbuf != null): the dot kernel also stores
+  // w_k = M r_k, and the update kernel forms s_k = M p_k by the recurrence
+  // s_k = w_k + beta s_{k-1} instead of gathering; r and p are updated in
+  // place (r[0] == r[1], p[0] == p[1]), s is kept in sbuf
+  T* wbuf;
+  T* sbuf;
 };
 
 // ---- handle -----------------------------------------------------------------
@@ -169,6 +175,7 @@ struct Handle {
   int opt_lanes = 0;
   int opt_cpl = 0;     // cap on column chunks per lane (0: kernel maximum)
   int opt_solver = 1;  // 0: COCG per shift, 1: multi-shift COCG (default)
+  int opt_update = 0;  // multi-shift update: 0 auto, 1 gathered products, 2 streamed
   // autotuned kernel shapes (lanes, chunks per lane) of the multi-shift
   // kernels, keyed by (pairs, shifts, precision)
   struct Shape {
@@ -229,6 +236,9 @@ template <typename T>
 void launch_ms_init(const CocgArgs<T>& a, int m_real, int num_sms, cudaStream_t s);
 template <typename T>
 void launch_ms_update(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s);
+// streamed multi-shift update (needs a.wbuf, a.sbuf; no gathers)
+template <typename T>
+void launch_ms_update_stream(const CocgArgs<T>& a, int num_sms, cudaStream_t s);
 int ms_max_cpl(bool fp64);
 // bulk-copy (TMA) kernels, float32, NC in {2, 4, 8}, blocked state layout
 // (kernels_tma.cu). which: 0 init, 1 dots, 2 update.

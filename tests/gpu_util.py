@@ -43,3 +43,11 @@ def rand_sym_csr(n, seed, density=0.02, dense_row=True, empty_rows=3):
     m.sort_indices()
     return (m.indptr.astype(np.int32), m.indices.astype(np.int32),
             m.data.astype(np.float64), m)
+
+
+def set_solver(lib, h, solver):
+    """0: one COCG per shift; 1: multi-shift COCG, update with gathered
+    products; 2: multi-shift COCG, streamed update."""
+    lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, 0 if solver == 0 else 1)
+    if solver:
+        lib.rafeast_set_option(h, lib.RAFEAST_OPT_UPDATE, 1 if solver == 1 else 2)

@@ -4,7 +4,7 @@ ARPACK) and with the oracle, on the small workloads: plain FEAST FP64 on the
 import numpy as np
 import pytest
 
-from gpu_util import colmajor_dev
+from gpu_util import colmajor_dev, set_solver
 from oracle import exact as E
 from oracle import feast as OF
 from oracle import metrics as M
@@ -60,13 +60,13 @@ def knn8k():
     return lap, g, w, v
 
 
-@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("solver", [0, 1, 2])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_knn8k_rafeast(lib, knn8k, prec, solver):
     lap, g, w, v = knn8k
     cfg = CF.CONFIGS["knn8k"]
     h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
-    lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, solver)
+    set_solver(lib, h, solver)
     try:
         lib.rafeast_warmstart(h, g["lmin"], g["lmax"], cfg.m0, cfg.p, cfg.q, cfg.seed)
         p = lib.RAFEAST_FP64 if prec == "fp64" else lib.RAFEAST_MIXED

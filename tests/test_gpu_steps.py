@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from gpu_util import colmajor_dev, from_colmajor, rand_sym_csr, to_dev
+from gpu_util import colmajor_dev, from_colmajor, rand_sym_csr, to_dev, set_solver
 from oracle import exact as E
 from oracle import feast as OF
 from oracle import metrics as M
@@ -192,17 +192,18 @@ def _filter_case():
     return lap, lmin, lmax
 
 
-@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("solver", [0, 1, 2])
 @pytest.mark.parametrize("form", ["direct", "correction"])
 @pytest.mark.parametrize("nc,e", [(1, 1.0), (2, 1.0), (3, 0.5), (4, 1.0), (5, 0.3), (8, 1.0)])
 def test_filter_fp64(lib, form, nc, e, solver):
-    """solver 0: one COCG per shift; 1: multi-shift COCG (one seed recurrence
-    per column, the other shifts from its scalars)."""
+    """solver 0: one COCG per shift; 1, 2: multi-shift COCG (one seed
+    recurrence per column, the other shifts from its scalars) with the
+    gathering and the streamed update kernel."""
     import torch
     lap, lmin, lmax = _filter_case()
     m0 = 11
     h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
-    lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, solver)
+    set_solver(lib, h, solver)
     try:
         q0 = OF.random_start(lap.n, m0, 3)
         z, w = OQ.nodes(lmin, lmax, nc, e)
@@ -221,7 +222,7 @@ def test_filter_fp64(lib, form, nc, e, solver):
         lib.rafeast_destroy(h)
 
 
-@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("solver", [0, 1, 2])
 @pytest.mark.parametrize("form", ["direct", "correction"])
 @pytest.mark.parametrize("nc", [2, 4])
 def test_filter_mixed(lib, form, nc, solver):
@@ -229,7 +230,7 @@ def test_filter_mixed(lib, form, nc, solver):
     lap, lmin, lmax = _filter_case()
     m0 = 11
     h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
-    lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, solver)
+    set_solver(lib, h, solver)
     try:
         q0 = OF.random_start(lap.n, m0, 3)
         z, w = OQ.nodes(lmin, lmax, nc, 1.0)
@@ -276,8 +277,8 @@ def _filter_complex64(A, q0, z, w, steps):
 @pytest.mark.parametrize("mat", ["grid", "adversarial"])
 @pytest.mark.parametrize("m0,nc", [(5, 2), (33, 4), (40, 3), (80, 4), (96, 8), (70, 2)])
 def test_gather_kernels_match_oracle_stepwise(lib, mat, m0, nc):
-    """After a fixed number of COCG steps (no convergence test) both gather
-    kernels reproduce the oracle's iterate: a wrong alpha/beta would still
+    """After a fixed number of COCG steps (no convergence test) every COCG
+    kernel variant reproduces the oracle's iterate: a wrong alpha/beta would still
     converge, so only a fixed step count exposes it. The adversarial matrix
     has empty rows (no diagonal entry) and a dense row spanning many copy
     items; block widths are not multiples of 32. Tolerance: float32 cannot
@@ -312,17 +313,19 @@ def test_gather_kernels_match_oracle_stepwise(lib, mat, m0, nc):
         f32 = np.linalg.norm(_filter_complex64(A, q0, z, w, 12) - exp) / scale
         tol = max(5e-5, 2.0 * f32)
         errs = {}
-        for kern in (1, 2, 3):
+        for kern in (1, 2, 3, 4):
             # 1 register gathers, 2 bulk-copy gathers, 3 multi-shift solver
+            # (gathering update), 4 multi-shift solver (streamed update)
             lib.rafeast_set_option(h, lib.RAFEAST_OPT_KERNEL, 2 if kern == 2 else 1)
-            lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, 1 if kern == 3 else 0)
+            lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, 1 if kern >= 3 else 0)
+            lib.rafeast_set_option(h, lib.RAFEAST_OPT_UPDATE, 2 if kern == 4 else 1)
             Qt = torch.zeros_like(Q)
             prm = lib.make_params(lo, hi, m0, nc, 1.0, 0.0, 1e-10, 1, 12, lib.RAFEAST_MIXED,
                                   lib.RAFEAST_FORM_CORRECTION)
             info = lib.rafeast_filter(h, prm, Q, None, Qt)
             assert info.cocg_max_last == 12
             errs[kern] = np.linalg.norm(from_colmajor(Qt) - exp) / scale
-        assert errs[1] <= tol and errs[2] <= tol and errs[3] <= tol, (errs, f32)
+        assert all(e <= tol for e in errs.values()), (errs, f32)
     finally:
         lib.rafeast_destroy(h)
 
