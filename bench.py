@@ -637,7 +637,7 @@ def main():
     peak, peak_kind = _peaks()
     # multi-shift COCG (default): seed dot kernel k_cocg_dots<.., 2, ..> and
     # k_ms_update; names of the ncu summaries under profiles/
-    names = {"update": "ms_update", "dots": "ms_dots"}
+    names = {"update": "ms_update_stream", "dots": "ms_dots"}
     pre = "update" if prof["update_ms"] >= prof["dots_ms"] else "dots"
     kern = names[pre]
     launches_k = max(prof[f"{pre}_launches"], 1.0)

@@ -412,11 +412,17 @@ static void dispatch_ms_update(const CocgArgs<T>& a, int buf, int num_sms, cudaS
   const size_t smem = (size_t)2 * a.lanes * a.cpl * (sizeof(Coef<T>) + NS * sizeof(ShiftCoef<T>)) + 16;
   const int colblocks = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);
   const int64_t groups = (a.n + (int64_t)WARPS * (32 / a.lanes) - 1) / ((int64_t)WARPS * (32 / a.lanes));
-  if (sizeof(T) == 4 && a.occ >= 3 && a.cpl <= MCS) {
-    auto kern = a.occ >= 4 ? k_ms_update_occ<T, NS, MCS, 4> : k_ms_update_occ<T, NS, MCS, 3>;
-    if (smem > 48 * 1024) ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
-    dim3 grid(grid_x(kern, smem, num_sms, groups), colblocks);
-    kern<<<grid, THREADS, smem, s>>>(a, buf);
+  bool done = false;
+  if constexpr (sizeof(T) == 4) {
+    if (a.occ >= 3 && a.cpl <= MCS) {
+      auto kern = a.occ >= 4 ? k_ms_update_occ<T, NS, MCS, 4> : k_ms_update_occ<T, NS, MCS, 3>;
+      if (smem > 48 * 1024) ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
+      dim3 grid(grid_x(kern, smem, num_sms, groups), colblocks);
+      kern<<<grid, THREADS, smem, s>>>(a, buf);
+      done = true;
+    }
+  }
+  if (done) {
   } else if (a.cpl <= MCS) {
     auto kern = k_ms_update<T, NS, MCS>;
     if (smem > 48 * 1024) ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
@@ -557,8 +563,9 @@ __global__ void __launch_bounds__(THREADS) k_spmm_real(int64_t n, const int32_t*
 template <typename T, int NC, int MC>
 static void dispatch_dots_mc(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
   auto kern = k_cocg_dots<T, NC, MC>;
-  if (NC == 2 && MC == 2 && sizeof(T) == 4 && a.occ >= 3)
-    kern = a.occ >= 4 ? k_cocg_dots_occ<T, MC, 4> : k_cocg_dots_occ<T, MC, 3>;
+  if constexpr (NC == 2 && MC == 2 && sizeof(T) == 4) {
+    if (a.occ >= 3) kern = a.occ >= 4 ? k_cocg_dots_occ<T, MC, 4> : k_cocg_dots_occ<T, MC, 3>;
+  }
   const size_t smem = (size_t)a.lanes * MC * NC * 5 * sizeof(double);
   const int colblocks = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);
   const int64_t groups = (a.n + (int64_t)WARPS * (32 / a.lanes) - 1) / ((int64_t)WARPS * (32 / a.lanes));
