@@ -103,7 +103,7 @@ extern "C" {
                                      * streamed (the dot kernel stores M r_k, *
                                      * M p_k follows by its recurrence; no    *
                                      * gathers in the update). Batched solves *
-                                     * use the gathered form.                 */
+                                     * follow the first handle's setting.     */
 #define RAFEAST_OPT_TEST_STALL 9    /* test hook: bytes (multiple of 16) that  *
                                      * every bulk-copy stage waits for and no *
                                      * copy delivers, so the bounded wait     *

@@ -856,7 +856,7 @@ static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cud
   for (int t = 0; t < cnt; ++t) {
     Handle* h = items[t]->h;
     P[t] = ms_setup<T>(h, *items[t]->prm, h->Q, h->AQ, h->theta_d, h->theta, h->m0, h->ldq,
-                       ctl_d + t, owner->opt_profile != 0, false, bs);
+                       ctl_d + t, owner->opt_profile != 0, owner->opt_update != 1, bs);
   }
   GroupDev<T> gd;
   gd.args_d = (const CocgArgs<T>*)(bb + o_ad);
@@ -1033,8 +1033,9 @@ static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cud
         if (k >= iters) continue;
         const int act_d = k == 0 ? P[t].pairs : hist[t][k - 1];
         const int act_u = hist[t][k];
-        bd += ms_dots_bytes(items[t]->h, act_d, fp64);
-        if (act_u > 0) bu += ms_update_bytes(items[t]->h, act_u, P[t].ns, fp64);
+        const bool st = P[t].a.wbuf != nullptr;
+        bd += ms_dots_bytes(items[t]->h, act_d, fp64, st);
+        if (act_u > 0) bu += ms_update_bytes(items[t]->h, act_u, P[t].ns, fp64, st);
         if (act_d > 0) ++probs;
         pairs_act += act_d;
       }

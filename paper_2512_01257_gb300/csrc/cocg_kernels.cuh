@@ -364,4 +364,98 @@ __device__ __forceinline__ void ms_update_body(const CocgArgs<T>& a, const CocgA
   }
 }
 
+// ---------------------------------------------------------------------------
+// streamed multi-shift update: one thread per (row, column pair), no
+// gathers. With w_k = M r_k stored by the dot kernel and s_{k-1} = M p_{k-1}
+// kept from the previous step:
+//   p_k = ar r_k + beta p_{k-1},  s_k = ar w_k + beta s_{k-1} (= M p_k),
+//   r_{k+1} = r_k - alpha s_k,    D += Re(c alpha p_k),
+// and the shifted directions p_j^k = zeta_k r_k + beta_j p_j^{k-1} as in the
+// gathering update. A frozen column has ar = 0, beta = 1, alpha = 0: its
+// state is left as it is. Every access is to the thread's own row.
+// ---------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ inline size_t ms_stream_smem(int pairs, int ns) {
+  return (size_t)2 * pairs * (sizeof(Coef<T>) + ns * sizeof(ShiftCoef<T>)) +
+         sizeof(int) * pairs + 16;
+}
+
+// the problem's coefficients and column activity into shared memory
+template <typename T, int NS>
+__device__ __forceinline__ void ms_stream_stage(const CocgArgs<T>& a, unsigned char* smem) {
+  const int P = a.m0;
+  Coef<T>* scf = reinterpret_cast<Coef<T>*>(smem);
+  ShiftCoef<T>* ssc = reinterpret_cast<ShiftCoef<T>*>(smem + sizeof(Coef<T>) * 2 * P);
+  int* sact = reinterpret_cast<int*>(smem + (sizeof(Coef<T>) + NS * sizeof(ShiftCoef<T>)) * 2 * P);
+  for (int t = threadIdx.x; t < 2 * P; t += blockDim.x) scf[t] = a.cf[t];
+  if (NS > 0)
+    for (int t = threadIdx.x; t < 2 * P * NS; t += blockDim.x) ssc[t] = a.scf[t];
+  for (int t = threadIdx.x; t < P; t += blockDim.x) sact[t] = __ldcg(a.colact + t);
+  __syncthreads();
+}
+
+// elements e0, e0 + step, ... < e1 of the n x pairs element grid
+template <typename T, int NS>
+__device__ __forceinline__ void ms_stream_elems(const CocgArgs<T>& a, const unsigned char* smem,
+                                                int64_t e0, int64_t e1, int64_t step) {
+  using C = c2<T>;
+  const int P = a.m0;
+  const Coef<T>* scf = reinterpret_cast<const Coef<T>*>(smem);
+  const ShiftCoef<T>* ssc =
+      reinterpret_cast<const ShiftCoef<T>*>(smem + sizeof(Coef<T>) * 2 * P);
+  const int* sact = reinterpret_cast<const int*>(
+      smem + (sizeof(Coef<T>) + NS * sizeof(ShiftCoef<T>)) * 2 * P);
+  T* __restrict__ R = a.r[0];
+  T* __restrict__ Pd = a.p[0];
+  const T* __restrict__ W = a.wbuf;
+  T* __restrict__ S = a.sbuf;
+  for (int64_t e = e0; e < e1; e += step) {
+    const int64_t row = e / P;
+    const int q = (int)(e - row * P);
+    if (!sact[q]) continue;
+    const int64_t off = (row * a.ldc + 2 * q) * 2;
+    C rv[2], pv[2], wv[2], sv[2], rn[2];
+    ld_chunk<2>(R + off, rv);
+    ld_chunk<2>(Pd + off, pv);
+    ldcg_chunk<2>(W + off, wv);
+    ld_chunk<2>(S + off, sv);
+    T dsum[2] = {(T)0, (T)0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const Coef<T> cf = scf[2 * q + h];
+      const C pn = cfma<T>(cf.beta, pv[h], mk<T>(cf.ar * rv[h].x, cf.ar * rv[h].y));
+      const C sn = cfma<T>(cf.beta, sv[h], mk<T>(cf.ar * wv[h].x, cf.ar * wv[h].y));
+      rn[h] = csub<T>(rv[h], cmul<T>(cf.alpha, sn));
+      pv[h] = pn;
+      sv[h] = sn;
+      dsum[h] = fma(cf.ca.x, pn.x, fma(-cf.ca.y, pn.y, dsum[h]));
+    }
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const ShiftCoef<T> s0 = ssc[(2 * q) * NS + t];
+      const ShiftCoef<T> s1 = ssc[(2 * q + 1) * NS + t];
+      if (s0.act != (T)0 || s1.act != (T)0) {
+        T* pp = a.ps + (row * a.ldps + 2 * ((int64_t)q * NS + t)) * 2;
+        C pj[2];
+        ldcg_chunk<2>(pp, pj);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const ShiftCoef<T>& sc = hh ? s1 : s0;
+          if (sc.act != (T)0) {
+            pj[hh] = cfma<T>(sc.beta, pj[hh], cmul<T>(sc.zeta, rv[hh]));
+            dsum[hh] = fma(sc.ca.x, pj[hh].x, fma(-sc.ca.y, pj[hh].y, dsum[hh]));
+          }
+        }
+        st_chunk<2>(pp, pj);
+      }
+    }
+    st_chunk<2>(R + off, rn);
+    st_chunk<2>(Pd + off, pv);
+    st_chunk<2>(S + off, sv);
+    T* dp = a.dacc + row * a.ldd + 2 * q;
+    dp[0] += dsum[0];
+    dp[1] += dsum[1];
+  }
+}
+
 }  // namespace rafeast

@@ -233,6 +233,34 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1)
   }
 }
 
+// streamed update over a queue of items: an item is a contiguous range of
+// one problem's n x pairs (row, column pair) elements; the problem's
+// coefficients are staged in shared memory per item (buf is unused: the
+// streamed state is updated in place)
+template <typename T, int NS>
+__global__ void __launch_bounds__(THREADS)
+    k_ms_update_stream_grouped(const CocgArgs<T>* __restrict__ args, const int* __restrict__ map,
+                               GroupCtl* __restrict__ gc, int count, int buf) {
+  (void)buf;
+  __shared__ int smap[2 * SMEM_MAP + 1];
+  extern __shared__ unsigned char smem_raw[];
+  const MapView m = stage_map(map, count, smap);
+  const int total = m[count];
+  for (;;) {
+    const int item = next_item(&gc->next_u, total);
+    if (item < 0) break;
+    const int t = item_owner(m, count, item);
+    const CocgArgs<T> a = args[t];
+    const Blk b = item_blk(m, count, t, item);
+    ms_stream_stage<T, NS>(a, smem_raw);
+    const int64_t tot = a.n * (int64_t)a.m0;
+    const int64_t chunk = (tot + b.gx - 1) / b.gx;
+    const int64_t e0 = b.x * chunk;
+    const int64_t e1 = e0 + chunk < tot ? e0 + chunk : tot;
+    ms_stream_elems<T, NS>(a, smem_raw, e0 + threadIdx.x, e1, blockDim.x);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -254,6 +282,21 @@ static const void* update_fn_ns(int ns) {
     case 5: return update_fn<T, 5, MC>();
     case 6: return update_fn<T, 6, MC>();
     case 7: return update_fn<T, 7, MC>();
+    default: throw Err{RAFEAST_ERR_INVALID_ARG};
+  }
+}
+
+template <typename T>
+static const void* stream_fn(int ns) {
+  switch (ns) {
+    case 0: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 0>);
+    case 1: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 1>);
+    case 2: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 2>);
+    case 3: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 3>);
+    case 4: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 4>);
+    case 5: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 5>);
+    case 6: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 6>);
+    case 7: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 7>);
     default: throw Err{RAFEAST_ERR_INVALID_ARG};
   }
 }
@@ -329,18 +372,38 @@ void plan_ms_grouped(const std::vector<CocgArgs<T>>& args_d, const std::vector<C
     ld = std::max(ld, a.lanes);
     lcu = std::max(lcu, b.lanes * b.cpl);
   }
+  const bool stream = args_u[0].wbuf != nullptr;
+  int pmax = 1;
+  for (int t = 0; t < cnt; ++t) {
+    RF_CHECK((args_u[t].wbuf != nullptr) == stream && (args_d[t].wbuf != nullptr) == stream,
+             RAFEAST_ERR_INVALID_ARG);
+    pmax = std::max(pmax, args_u[t].m0);
+  }
   g.mc_d = cd <= 2 ? 2 : grouped_mc_large<T>();
   g.mc_u = cu <= 2 ? 2 : grouped_mc_large<T>();
   g.smem_dots = (size_t)ld * g.mc_d * 2 * 5 * sizeof(double);
-  g.smem_upd = (size_t)2 * lcu * (sizeof(Coef<T>) + g.ns * sizeof(ShiftCoef<T>)) + 16;
   g.fn_dots = dots_fn<T>(g.mc_d);
-  g.fn_upd = upd_fn<T>(g.mc_u, g.ns);
+  if (stream) {
+    g.smem_upd = ms_stream_smem<T>(pmax, g.ns);
+    g.fn_upd = stream_fn<T>(g.ns);
+  } else {
+    g.smem_upd = (size_t)2 * lcu * (sizeof(Coef<T>) + g.ns * sizeof(ShiftCoef<T>)) + 16;
+    g.fn_upd = upd_fn<T>(g.mc_u, g.ns);
+  }
   if (g.smem_upd > 48 * 1024) ensure_dyn_smem(g.fn_upd, g.smem_upd);
   int occ_d = 0, occ_u = 0;
   RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, g.fn_dots, THREADS, g.smem_dots));
   RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, g.fn_upd, THREADS, g.smem_upd));
   shapes_of(args_d, g.gg_d);
   shapes_of(args_u, g.gg_u);
+  if (stream)
+    for (int t = 0; t < cnt; ++t) {
+      // element passes of one CTA over the problem's n x pairs elements
+      const int64_t el = args_u[t].n * (int64_t)args_u[t].m0;
+      RF_CHECK((el + THREADS - 1) / THREADS < 0x7fffffff, RAFEAST_ERR_INVALID_ARG);
+      g.gg_u[4 * t] = (int)((el + THREADS - 1) / THREADS);
+      g.gg_u[4 * t + 1] = 1;
+    }
   long long wkb = 0;
   for (int t = 0; t < cnt; ++t) wkb += g.gg_d[4 * t + 2];
   g.ctas_dots = num_sms * std::max(occ_d, 1);

@@ -294,88 +294,18 @@ __global__ void __launch_bounds__(THREADS, MINB) k_cocg_dots_occ(CocgArgs<T> a, 
   cocg_dots_body<T, 2, MAXCPL>(a, &a, buf, grid_blk());
 }
 
-// streamed multi-shift update: one thread per (row, column pair), no
-// gathers. With w_k = M r_k stored by the dot kernel and s_{k-1} = M p_{k-1}
-// kept from the previous step:
-//   p_k = ar r_k + beta p_{k-1},  s_k = ar w_k + beta s_{k-1} (= M p_k),
-//   r_{k+1} = r_k - alpha s_k,    D += Re(c alpha p_k),
-// and the shifted directions p_j^k = zeta_k r_k + beta_j p_j^{k-1} as in the
-// gathering update. A frozen column has ar = 0, beta = 1, alpha = 0: its
-// state is left as it is. Every access is to the thread's own row.
 template <typename T, int NS>
 __global__ void __launch_bounds__(THREADS) k_ms_update_stream(CocgArgs<T> a) {
-  using C = c2<T>;
   if (__ldcg(&a.ctl->done)) return;
-  const int P = a.m0;  // column pairs
   extern __shared__ unsigned char smem_raw[];
-  Coef<T>* scf = reinterpret_cast<Coef<T>*>(smem_raw);
-  ShiftCoef<T>* ssc = reinterpret_cast<ShiftCoef<T>*>(smem_raw + sizeof(Coef<T>) * 2 * P);
-  int* sact = reinterpret_cast<int*>(smem_raw +
-                                     (sizeof(Coef<T>) + NS * sizeof(ShiftCoef<T>)) * 2 * P);
-  for (int t = threadIdx.x; t < 2 * P; t += blockDim.x) scf[t] = a.cf[t];
-  if (NS > 0)
-    for (int t = threadIdx.x; t < 2 * P * NS; t += blockDim.x) ssc[t] = a.scf[t];
-  for (int t = threadIdx.x; t < P; t += blockDim.x) sact[t] = __ldcg(a.colact + t);
-  __syncthreads();
-  T* __restrict__ R = a.r[0];
-  T* __restrict__ Pd = a.p[0];
-  const T* __restrict__ W = a.wbuf;
-  T* __restrict__ S = a.sbuf;
-  const int64_t total = a.n * (int64_t)P;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = e / P;
-    const int q = (int)(e - row * P);
-    if (!sact[q]) continue;
-    const int64_t off = (row * a.ldc + 2 * q) * 2;
-    C rv[2], pv[2], wv[2], sv[2], rn[2];
-    ld_chunk<2>(R + off, rv);
-    ld_chunk<2>(Pd + off, pv);
-    ldcg_chunk<2>(W + off, wv);
-    ld_chunk<2>(S + off, sv);
-    T dsum[2] = {(T)0, (T)0};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const Coef<T> cf = scf[2 * q + h];
-      const C pn = cfma<T>(cf.beta, pv[h], mk<T>(cf.ar * rv[h].x, cf.ar * rv[h].y));
-      const C sn = cfma<T>(cf.beta, sv[h], mk<T>(cf.ar * wv[h].x, cf.ar * wv[h].y));
-      rn[h] = csub<T>(rv[h], cmul<T>(cf.alpha, sn));
-      pv[h] = pn;
-      sv[h] = sn;
-      dsum[h] = fma(cf.ca.x, pn.x, fma(-cf.ca.y, pn.y, dsum[h]));
-    }
-#pragma unroll
-    for (int t = 0; t < NS; ++t) {
-      const ShiftCoef<T> s0 = ssc[(2 * q) * NS + t];
-      const ShiftCoef<T> s1 = ssc[(2 * q + 1) * NS + t];
-      if (s0.act != (T)0 || s1.act != (T)0) {
-        T* pp = a.ps + (row * a.ldps + 2 * ((int64_t)q * NS + t)) * 2;
-        C pj[2];
-        ldcg_chunk<2>(pp, pj);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const ShiftCoef<T>& sc = h ? s1 : s0;
-          if (sc.act != (T)0) {
-            pj[h] = cfma<T>(sc.beta, pj[h], cmul<T>(sc.zeta, rv[h]));
-            dsum[h] = fma(sc.ca.x, pj[h].x, fma(-sc.ca.y, pj[h].y, dsum[h]));
-          }
-        }
-        st_chunk<2>(pp, pj);
-      }
-    }
-    st_chunk<2>(R + off, rn);
-    st_chunk<2>(Pd + off, pv);
-    st_chunk<2>(S + off, sv);
-    T* dp = a.dacc + row * a.ldd + 2 * q;
-    dp[0] += dsum[0];
-    dp[1] += dsum[1];
-  }
+  ms_stream_stage<T, NS>(a, smem_raw);
+  ms_stream_elems<T, NS>(a, smem_raw, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                         a.n * (int64_t)a.m0, (int64_t)gridDim.x * blockDim.x);
 }
 
 template <typename T, int NS>
 static void dispatch_ms_update_stream(const CocgArgs<T>& a, int num_sms, cudaStream_t s) {
-  const size_t smem = (size_t)2 * a.m0 * (sizeof(Coef<T>) + NS * sizeof(ShiftCoef<T>)) +
-                      sizeof(int) * a.m0 + 16;
+  const size_t smem = ms_stream_smem<T>(a.m0, NS);
   auto kern = k_ms_update_stream<T, NS>;
   if (smem > 48 * 1024) ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
   int occ = 0;

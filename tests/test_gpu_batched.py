@@ -61,9 +61,13 @@ def _run_batched(lib, hs, probs, prms):
     return st, mf, info, ev, vec, res
 
 
+@pytest.mark.parametrize("update", [1, 2])
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_batched_sbm_against_lanczos(lib, sbm6, prec):
+def test_batched_sbm_against_lanczos(lib, sbm6, prec, update):
+    """update 1: grouped gathering update; 2: grouped streamed update (the
+    first handle's option decides for the batch)."""
     hs = _handles(lib, sbm6)
+    lib.rafeast_set_option(hs[0], lib.RAFEAST_OPT_UPDATE, update)
     try:
         prms = [_params(lib, pr, prec, solve_tol=1e-2 if prec == "mixed" else 1e-4,
                         max_inner=100 if prec == "mixed" else 2000) for pr in sbm6]
