@@ -429,11 +429,15 @@ void chol_inv(double* G, int m, int64_t nrows, double* Rfac, double* Rinv, int* 
 
 // ---------------------------------------------------------------------------
 // one-CTA cyclic Jacobi (round-robin parallel order)
+constexpr size_t JACOBI_SMEM_MAX = 216 * 1024;  // A and V in shared memory up to me = 116
 // ---------------------------------------------------------------------------
 __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restrict__ w,
-                         double* __restrict__ Vout, double* __restrict__ Vw, int max_sweeps) {
-  extern __shared__ double A[];  // me * me, me = m rounded up to even
+                         double* __restrict__ Vout, double* __restrict__ Vg, int max_sweeps) {
+  extern __shared__ double A[];  // me * me (+ me * me for V when it fits)
   const int me = m + (m & 1);
+  // the eigenvector accumulator in shared memory when both fit, else in the
+  // global work buffer
+  double* Vw = (2 * (size_t)me * me * sizeof(double) <= JACOBI_SMEM_MAX) ? A + me * me : Vg;
   __shared__ double cs[64 * 2];  // c, s per pair (me/2 <= 64)
   __shared__ int pq[64 * 2];
   __shared__ double s_off, s_tot;
@@ -495,36 +499,37 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
         pq[2 * k + 1] = q;
       }
       __syncthreads();
-      // rows: (J^T A)
-      for (int t = threadIdx.x; t < np * me; t += blockDim.x) {
-        const int k = t / me, col = t % me;
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        if (s == 0.0) continue;
-        const int p = pq[2 * k], q = pq[2 * k + 1];
-        const double ap = A[p * me + col], aq = A[q * me + col];
-        A[p * me + col] = c * ap - s * aq;
-        A[q * me + col] = s * ap + c * aq;
+      // the pairs of a round are disjoint, so every 2 x 2 block (rows of
+      // pair j, columns of pair k) is updated on its own from its old
+      // values: B <- L_j B R_k with L = [[c, -s], [s, c]], R = L^T; the
+      // rotated diagonal blocks lose their off-diagonal entry
+      for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+        const int j = t / np, k = t % np;
+        const double cj = cs[2 * j], sj = cs[2 * j + 1];
+        const double ck = cs[2 * k], sk = cs[2 * k + 1];
+        if (sj == 0.0 && sk == 0.0) continue;
+        const int pj = pq[2 * j], qj = pq[2 * j + 1];
+        const int pk = pq[2 * k], qk = pq[2 * k + 1];
+        const double a11 = A[pj * me + pk], a12 = A[pj * me + qk];
+        const double a21 = A[qj * me + pk], a22 = A[qj * me + qk];
+        // rows: L_j B
+        const double b11 = cj * a11 - sj * a21, b12 = cj * a12 - sj * a22;
+        const double b21 = sj * a11 + cj * a21, b22 = sj * a12 + cj * a22;
+        // columns: (L_j B) R_k
+        A[pj * me + pk] = ck * b11 - sk * b12;
+        A[pj * me + qk] = j == k ? 0.0 : sk * b11 + ck * b12;
+        A[qj * me + pk] = j == k ? 0.0 : ck * b21 - sk * b22;
+        A[qj * me + qk] = sk * b21 + ck * b22;
       }
-      __syncthreads();
-      // columns: (A J) and V J
+      // V R_k
       for (int t = threadIdx.x; t < np * me; t += blockDim.x) {
         const int k = t / me, row = t % me;
         const double c = cs[2 * k], s = cs[2 * k + 1];
         if (s == 0.0) continue;
         const int p = pq[2 * k], q = pq[2 * k + 1];
-        const double ap = A[row * me + p], aq = A[row * me + q];
-        A[row * me + p] = c * ap - s * aq;
-        A[row * me + q] = s * ap + c * aq;
         const double vp = Vw[row * me + p], vq = Vw[row * me + q];
         Vw[row * me + p] = c * vp - s * vq;
         Vw[row * me + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-      for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        if (cs[2 * k + 1] == 0.0) continue;
-        const int p = pq[2 * k], q = pq[2 * k + 1];
-        A[p * me + q] = 0.0;
-        A[q * me + p] = 0.0;
       }
       __syncthreads();
     }
@@ -554,7 +559,8 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
 void jacobi_eigh(double* A, int m, double* w, double* V, double* work, cudaStream_t s) {
   if (m > 128) throw Err{RAFEAST_ERR_INVALID_ARG};
   const int me = m + (m & 1);
-  const size_t smem = (size_t)me * me * sizeof(double);
+  size_t smem = (size_t)me * me * sizeof(double);
+  if (2 * smem <= JACOBI_SMEM_MAX) smem *= 2;  // V beside A
   ensure_dyn_smem(reinterpret_cast<const void*>(k_jacobi), smem);
   k_jacobi<<<1, 512, smem, s>>>(A, m, w, V, work, 40);
   RF_LAUNCH();

@@ -158,7 +158,7 @@ def test_gram(lib, m):
 
 # ---- a9/a10: Rayleigh-Ritz and residuals -----------------------------------------
 
-@pytest.mark.parametrize("m", [1, 6, 31, 80, 116])
+@pytest.mark.parametrize("m", [1, 6, 31, 80, 116, 127])
 def test_rayleigh_ritz(lib, m):
     lap = G.knn3d(1800, 8, seed=11, shift=1e-3)
     h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
