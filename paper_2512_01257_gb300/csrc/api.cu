@@ -1934,15 +1934,28 @@ int rafeast_warmstart(rafeast_t hh, double lmin, double lmax, int m0, int p, int
     h->spmm_launches += 2;
   }
   cholqr(h, Y, Z, k, ld, nullptr);
-  // Rayleigh-Ritz on the m0+p columns
-  double* Qall = (double*)scratch(h, S_QT, sizeof(double) * h->n * ld);
-  double* AQall = (double*)scratch(h, S_AQ2, sizeof(double) * h->n * ld);
+  // Rayleigh-Ritz on the m0+p columns: A_Y = Y^T A Y, eigh, and only the m0
+  // Ritz vectors kept are formed (Y V_sel and (A Y) V_sel)
+  double* AY = (double*)scratch(h, S_AQ2, sizeof(double) * h->n * ld);
   double* th_all = (double*)scratch(h, S_IO1, sizeof(double) * (k + 1));
-  rayleigh_ritz_dev(h, Y, k, ld, Qall, AQall, th_all, Z);
-  std::vector<double> th(k);
-  RF_CUDA(cudaMemcpyAsync(th.data(), th_all, sizeof(double) * k, cudaMemcpyDeviceToHost,
-                          h->stream));
-  RF_CUDA(cudaStreamSynchronize(h->stream));
+  {
+    DenseWs d = dense_ws(h, k);
+    launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, k, ld, 1.0, h->shift, Y, AY,
+                             h->num_sms, h->stream);
+    gram(Y, AY, h->n, k, ld, d.G, d.part, h->num_sms, h->stream);
+    jacobi_eigh(d.G, k, th_all, d.V, d.Vw, h->stream);
+    h->launches += 4;
+    h->spmm_launches += 1;
+  }
+  std::vector<double> th(k), V((size_t)k * k);
+  {
+    DenseWs d = dense_ws(h, k);
+    RF_CUDA(cudaMemcpyAsync(th.data(), th_all, sizeof(double) * k, cudaMemcpyDeviceToHost,
+                            h->stream));
+    RF_CUDA(cudaMemcpyAsync(V.data(), d.V, sizeof(double) * k * k, cudaMemcpyDeviceToHost,
+                            h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+  }
   // keep the m0 Ritz values closest to the interval centre (stable ties)
   const double c = 0.5 * (lmin + lmax);
   std::vector<int> idx(k);
@@ -1951,17 +1964,19 @@ int rafeast_warmstart(rafeast_t hh, double lmin, double lmax, int m0, int p, int
                    [&](int a, int b) { return std::fabs(th[a] - c) < std::fabs(th[b] - c); });
   idx.resize(m0);
   std::sort(idx.begin(), idx.end());
-  // selection matrix (k x m0) applied with the tall GEMM
+  // the kept eigenvector columns (k x m0, row-major) applied with the tall GEMM
   std::vector<double> S((size_t)k * m0, 0.0);
-  for (int j = 0; j < m0; ++j) S[(size_t)idx[j] * m0 + j] = 1.0;
+  for (int a = 0; a < k; ++a)
+    for (int j = 0; j < m0; ++j) S[(size_t)a * m0 + j] = V[(size_t)a * k + idx[j]];
   ensure_subspace_bufs(h, m0);
   DenseWs d = dense_ws(h, k);
   RF_CUDA(cudaMemcpyAsync(d.V, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice,
                           h->stream));
   RF_CUDA(cudaMemsetAsync(h->Q, 0, sizeof(double) * h->n * h->ldq, h->stream));
   RF_CUDA(cudaMemsetAsync(h->AQ, 0, sizeof(double) * h->n * h->ldq, h->stream));
-  tall_gemm(Qall, h->n, k, ld, d.V, m0, h->Q, h->ldq, h->stream);
-  tall_gemm(AQall, h->n, k, ld, d.V, m0, h->AQ, h->ldq, h->stream);
+  tall_gemm(Y, h->n, k, ld, d.V, m0, h->Q, h->ldq, h->stream);
+  tall_gemm(AY, h->n, k, ld, d.V, m0, h->AQ, h->ldq, h->stream);
+  h->launches += 2;
   h->theta.resize(m0);
   for (int j = 0; j < m0; ++j) h->theta[j] = th[idx[j]];
   RF_CUDA(cudaMemcpyAsync(h->theta_d, h->theta.data(), sizeof(double) * m0,
