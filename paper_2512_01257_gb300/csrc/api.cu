@@ -152,7 +152,7 @@ static int cholqr(Handle* h, double*& X, double*& tmp, int m, int ld, std::vecto
     for (int i = 0; i < m; ++i) Racc[i * m + i] = 1.0;
   }
   for (int pass = 0; pass < passes; ++pass) {
-    gram(X, X, h->n, m, ld, d.G, d.part, h->num_sms, h->stream);
+    gram(X, X, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true);
     chol_inv(d.G, m, h->n, d.R, d.Rinv, d.status, h->stream);
     h->launches += 3;
     int st = 0;
@@ -163,7 +163,7 @@ static int cholqr(Handle* h, double*& X, double*& tmp, int m, int ld, std::vecto
       ++shifted;
       if (passes < 4) ++passes;
     }
-    tall_gemm(X, h->n, m, ld, d.Rinv, m, tmp, ld, h->stream);
+    tall_gemm(X, h->n, m, ld, d.Rinv, m, tmp, ld, h->stream, true);
     h->launches += 1;
     std::swap(X, tmp);
     if (Rtot) {
@@ -192,7 +192,7 @@ static void rayleigh_ritz_dev(Handle* h, const double* X, int m, int ld, double*
   DenseWs d = dense_ws(h, m);
   launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m, ld, 1.0, h->shift, X, tmp,
                            h->num_sms, h->stream);
-  gram(X, tmp, h->n, m, ld, d.G, d.part, h->num_sms, h->stream);
+  gram(X, tmp, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true);
   jacobi_eigh(d.G, m, theta_d, d.V, d.Vw, h->stream);
   tall_gemm(X, h->n, m, ld, d.V, m, Qout, ld, h->stream);
   tall_gemm(tmp, h->n, m, ld, d.V, m, AQout, ld, h->stream);
@@ -1942,7 +1942,7 @@ int rafeast_warmstart(rafeast_t hh, double lmin, double lmax, int m0, int p, int
     DenseWs d = dense_ws(h, k);
     launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, k, ld, 1.0, h->shift, Y, AY,
                              h->num_sms, h->stream);
-    gram(Y, AY, h->n, k, ld, d.G, d.part, h->num_sms, h->stream);
+    gram(Y, AY, h->n, k, ld, d.G, d.part, h->num_sms, h->stream, true);
     jacobi_eigh(d.G, k, th_all, d.V, d.Vw, h->stream);
     h->launches += 4;
     h->spmm_launches += 1;

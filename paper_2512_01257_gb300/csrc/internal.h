@@ -315,10 +315,13 @@ void launch_from_internal(int64_t n, int m, const double* src, int ld, double* d
                           const int32_t* perm, const int32_t* cols /* may be null */,
                           cudaStream_t s);
 // row-major tall blocks, FP64
+// G = X^T Y (m x m, ld m); sym: X^T Y is symmetric (X^T X, X^T A X), only
+// one triangle of tile blocks is formed and mirrored
 void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
-          double* partial, int num_sms, cudaStream_t s);  // G = X^T Y (m x m, ld m)
+          double* partial, int num_sms, cudaStream_t s, bool sym = false);
+// Y = X * M (M: m x mo, ld mo); upper: M is upper triangular (m == mo)
 void tall_gemm(const double* X, int64_t n, int m, int ldx, const double* M, int mo,
-               double* Y, int ldy, cudaStream_t s);       // Y = X * M (M: m x mo, ld mo)
+               double* Y, int ldy, cudaStream_t s, bool upper = false);
 // one-CTA Cholesky of G (+shift when needed) and inverse of the factor:
 // Rinv (m x m, ld m, upper) with Q R = X -> Q = X Rinv. status[0] = 0 ok,
 // 1 shifted, 2 failed; status[1..] unused.

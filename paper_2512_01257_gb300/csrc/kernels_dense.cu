@@ -188,7 +188,9 @@ void launch_zero(void* p, size_t bytes, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 constexpr int GRAM_RB = 16;
 
-template <int U>
+// SYM: the result is symmetric, so the 16-strided tile blocks below the
+// diagonal (u > v) are skipped; k_gram_sum mirrors them
+template <int U, bool SYM>
 __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ X,
                                                       const double* __restrict__ Y, int64_t n,
                                                       int m, int ld, double* __restrict__ part) {
@@ -225,7 +227,8 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < U; ++v) acc[u][v] = fma(xa[u], yb[v], acc[u][v]);
+        for (int v = 0; v < U; ++v)
+          if (!SYM || u <= v) acc[u][v] = fma(xa[u], yb[v], acc[u][v]);
     }
   }
   double* out = part + (int64_t)blockIdx.x * m * m;
@@ -234,37 +237,48 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
 #pragma unroll
     for (int v = 0; v < U; ++v) {
       const int a = tx + 16 * u, b = ty + 16 * v;
-      if (a < m && b < m) out[a * m + b] = acc[u][v];
+      if (a < m && b < m && (!SYM || u <= v)) out[a * m + b] = acc[u][v];
     }
 }
 
-__global__ void k_gram_sum(const double* __restrict__ part, int nparts, int mm, double* G) {
+// sym: entries (a, b) with a / 16 > b / 16 were not computed; take (b, a)
+__global__ void k_gram_sum(const double* __restrict__ part, int nparts, int m, int sym,
+                           double* G) {
+  const int mm = m * m;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += gridDim.x * blockDim.x) {
+    const int a = e / m, b = e - a * m;
+    const int src = (sym && (a >> 4) > (b >> 4)) ? b * m + a : e;
     double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * mm + e];
+    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * mm + src];
     G[e] = s;
   }
 }
 
 int gram_parts(int num_sms) { return 2 * num_sms; }
 
-void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
-          double* partial, int num_sms, cudaStream_t s) {
-  const int U = (m + 15) / 16;
-  const int parts = gram_parts(num_sms);
-  const size_t smem = 2 * GRAM_RB * (size_t)ld * sizeof(double);
-  switch (U) {
+template <bool SYM>
+static void gram_partials(const double* X, const double* Y, int64_t n, int m, int ld,
+                          double* partial, int parts, size_t smem, cudaStream_t s) {
+  switch ((m + 15) / 16) {
 #define RF_GRAM(UU)                                                                   \
   case UU:                                                                            \
-    ensure_dyn_smem(reinterpret_cast<const void*>(k_gram_partial<UU>), smem);        \
-    k_gram_partial<UU><<<parts, 256, smem, s>>>(X, Y, n, m, ld, partial);             \
+    ensure_dyn_smem(reinterpret_cast<const void*>(k_gram_partial<UU, SYM>), smem);   \
+    k_gram_partial<UU, SYM><<<parts, 256, smem, s>>>(X, Y, n, m, ld, partial);        \
     break;
     RF_GRAM(1) RF_GRAM(2) RF_GRAM(3) RF_GRAM(4) RF_GRAM(5) RF_GRAM(6) RF_GRAM(7) RF_GRAM(8)
 #undef RF_GRAM
     default: throw Err{RAFEAST_ERR_INVALID_ARG};
   }
+}
+
+void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
+          double* partial, int num_sms, cudaStream_t s, bool sym) {
+  const int parts = gram_parts(num_sms);
+  const size_t smem = 2 * GRAM_RB * (size_t)ld * sizeof(double);
+  if (sym) gram_partials<true>(X, Y, n, m, ld, partial, parts, smem, s);
+  else gram_partials<false>(X, Y, n, m, ld, partial, parts, smem, s);
   RF_LAUNCH();
-  k_gram_sum<<<(m * m + 255) / 256, 256, 0, s>>>(partial, parts, m * m, G);
+  k_gram_sum<<<(m * m + 255) / 256, 256, 0, s>>>(partial, parts, m, sym ? 1 : 0, G);
   RF_LAUNCH();
 }
 
@@ -273,7 +287,9 @@ void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
 // ---------------------------------------------------------------------------
 constexpr int GEMM_ROWS = 8;
 
-template <int V>
+// UPPER: M is upper triangular (M[a][b] = 0 for a > b): column block v of
+// 32 columns needs rows a < 32 v + 32 only (a warp-uniform bound)
+template <int V, bool UPPER>
 __global__ void __launch_bounds__(256) k_tall_gemm(const double* __restrict__ X, int64_t n, int m,
                                                    int ldx, const double* __restrict__ M, int mo,
                                                    double* __restrict__ Y, int ldy) {
@@ -299,6 +315,7 @@ __global__ void __launch_bounds__(256) k_tall_gemm(const double* __restrict__ X,
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int b = tc + 32 * v;
+          if (UPPER && a >= 32 * v + 32) continue;
           if (b < mo) acc[v] = fma(x, Ms[a * mo + b], acc[v]);
         }
       }
@@ -312,7 +329,7 @@ __global__ void __launch_bounds__(256) k_tall_gemm(const double* __restrict__ X,
 }
 
 void tall_gemm(const double* X, int64_t n, int m, int ldx, const double* M, int mo, double* Y,
-               int ldy, cudaStream_t s) {
+               int ldy, cudaStream_t s, bool upper) {
   const int V = (mo + 31) / 32;
   const size_t smem = ((size_t)m * mo + (size_t)GEMM_ROWS * m) * sizeof(double);
   int dev = 0, sms = 0;
@@ -324,8 +341,13 @@ void tall_gemm(const double* X, int64_t n, int m, int ldx, const double* M, int 
   switch (V) {
 #define RF_TG(VV)                                                                     \
   case VV:                                                                            \
-    ensure_dyn_smem(reinterpret_cast<const void*>(k_tall_gemm<VV>), smem);           \
-    k_tall_gemm<VV><<<blocks, 256, smem, s>>>(X, n, m, ldx, M, mo, Y, ldy);           \
+    if (upper) {                                                                      \
+      ensure_dyn_smem(reinterpret_cast<const void*>(k_tall_gemm<VV, true>), smem);   \
+      k_tall_gemm<VV, true><<<blocks, 256, smem, s>>>(X, n, m, ldx, M, mo, Y, ldy);   \
+    } else {                                                                          \
+      ensure_dyn_smem(reinterpret_cast<const void*>(k_tall_gemm<VV, false>), smem);  \
+      k_tall_gemm<VV, false><<<blocks, 256, smem, s>>>(X, n, m, ldx, M, mo, Y, ldy);  \
+    }                                                                                 \
     break;
     RF_TG(1) RF_TG(2) RF_TG(3) RF_TG(4)
 #undef RF_TG
