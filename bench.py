@@ -246,7 +246,7 @@ def _reference_counts(key):
     # iteration counts of the GPU solve of this workload (same algorithm and
     # parameters); used only to extrapolate the oracle's bounded sample
     table = {"knn200k": dict(outer=8, cocg_total=800),
-             "grid3d": dict(outer=10, cocg_total=1000),
+             "grid3d": dict(outer=9, cocg_total=900),
              "knn8k": dict(outer=11, cocg_total=900)}
     return table[key]
 

@@ -18,7 +18,7 @@ too, so every consumer reads the same numbers.
   (COCG tolerance 1e-2, at most 100 steps), outer tolerance 1e-11.
 * ``grid3d``  RA-FEAST, mixed: 3-D 7-point grid 100^3 (n=1e6, nnz=6.94e6)
   + 1e-2 I, 63 eigenvalues in [0.005, 0.0272568], m0=96, N_c=4, p=20, q=2,
-  inner solves as ``knn200k``.
+  inner solves as ``knn200k``, outer tolerance 1e-10.
 * ``sbm64``   batched RA-FEAST, mixed: 64 stochastic-block-model Laplacians
   + 1e-3 I, n log-uniform in [2000, 300000] (seed 4), 4..16 blocks,
   p_in = 20/n_block, p_out = 1/n, k = blocks + 8, m0 = ceil(1.5 k), N_c=2;
@@ -75,8 +75,12 @@ def _cfgs():
         "knn200k": Config("knn200k", lambda: graphs.knn3d(200000, 10, 2, 1e-3), 64, 80, 4,
                           "mixed", 1e-2, 1e-11, "correction", True, p=20, q=2, seed=2,
                           max_inner=100, description="RA-FEAST mixed, kNN n=200000"),
+        # outer tolerance 1e-10: the measured residual sequence is 2.9e-10,
+        # 1.02e-11, 1.1e-12 at outer iterations 8, 9, 10, so 1e-11 would put the
+        # stopping step on the fourth digit of a residual (9 or 10 iterations
+        # by rounding); the eigenvalues are at 7e-14 relative error by then
         "grid3d": Config("grid3d", lambda: graphs.grid3d(100, 100, 100, 1e-2), 63, 96, 4,
-                         "mixed", 1e-2, 1e-11, "correction", True, p=20, q=2, seed=3,
+                         "mixed", 1e-2, 1e-10, "correction", True, p=20, q=2, seed=3,
                          max_inner=100, description="RA-FEAST mixed, 3-D grid 100^3"),
     }
 
