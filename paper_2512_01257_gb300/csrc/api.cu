@@ -185,8 +185,8 @@ static int cholqr(Handle* h, double*& X, double*& tmp, int m, int ld, std::vecto
   return shifted;
 }
 
-// Rayleigh-Ritz on X (n x m, ld, orthonormal): Qout = X V, AQout = (A X) V,
-// theta (device, m, ascending), resid2 (device, m).
+// Rayleigh-Ritz on X (n x m, ld, orthonormal): Qout = X V, AQout = A Qout,
+// theta (device, m, ascending).
 static void rayleigh_ritz_dev(Handle* h, const double* X, int m, int ld, double* Qout,
                               double* AQout, double* theta_d, double* tmp) {
   DenseWs d = dense_ws(h, m);
@@ -195,9 +195,11 @@ static void rayleigh_ritz_dev(Handle* h, const double* X, int m, int ld, double*
   gram(X, tmp, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true);
   jacobi_eigh(d.G, m, theta_d, d.V, d.Vw, h->stream);
   tall_gemm(X, h->n, m, ld, d.V, m, Qout, ld, h->stream);
-  tall_gemm(tmp, h->n, m, ld, d.V, m, AQout, ld, h->stream);
+  // A Q by the (memory-bound) SpMM rather than (A X) V by an FP64 GEMM
+  launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m, ld, 1.0, h->shift, Qout,
+                           AQout, h->num_sms, h->stream);
   h->launches += 7;
-  h->spmm_launches += 1;
+  h->spmm_launches += 2;
 }
 
 static void residuals_host(Handle* h, const double* Q, const double* AQ, const double* theta_d,
@@ -1935,7 +1937,7 @@ int rafeast_warmstart(rafeast_t hh, double lmin, double lmax, int m0, int p, int
   }
   cholqr(h, Y, Z, k, ld, nullptr);
   // Rayleigh-Ritz on the m0+p columns: A_Y = Y^T A Y, eigh, and only the m0
-  // Ritz vectors kept are formed (Y V_sel and (A Y) V_sel)
+  // Ritz vectors kept are formed (Q = Y V_sel, then A Q)
   double* AY = (double*)scratch(h, S_AQ2, sizeof(double) * h->n * ld);
   double* th_all = (double*)scratch(h, S_IO1, sizeof(double) * (k + 1));
   {
@@ -1975,8 +1977,10 @@ int rafeast_warmstart(rafeast_t hh, double lmin, double lmax, int m0, int p, int
   RF_CUDA(cudaMemsetAsync(h->Q, 0, sizeof(double) * h->n * h->ldq, h->stream));
   RF_CUDA(cudaMemsetAsync(h->AQ, 0, sizeof(double) * h->n * h->ldq, h->stream));
   tall_gemm(Y, h->n, k, ld, d.V, m0, h->Q, h->ldq, h->stream);
-  tall_gemm(AY, h->n, k, ld, d.V, m0, h->AQ, h->ldq, h->stream);
+  launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m0, h->ldq, 1.0, h->shift, h->Q,
+                           h->AQ, h->num_sms, h->stream);
   h->launches += 2;
+  h->spmm_launches += 1;
   h->theta.resize(m0);
   for (int j = 0; j < m0; ++j) h->theta[j] = th[idx[j]];
   RF_CUDA(cudaMemcpyAsync(h->theta_d, h->theta.data(), sizeof(double) * m0,
