@@ -722,7 +722,8 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
     // (lanes, chunks, CTAs per SM; 0 = the default instance)
     const int cand[][3] = {{32, 2, 0}, {16, 2, 0}, {16, 3, 0}, {16, 4, 0}, {8, 1, 0},
                            {8, 2, 0},  {8, 4, 0},  {4, 2, 0},  {32, 2, 3}, {16, 2, 3},
-                           {8, 2, 3},  {16, 2, 4}};
+                           {8, 2, 3},  {16, 2, 4}, {16, 3, 2}, {16, 4, 2}, {8, 3, 2},
+                           {8, 4, 2},  {16, 3, 3}};
     float best_d = 1e30f, best_u = 1e30f;
     for (auto& c : cand) {
       if (ctl.done) break;

@@ -496,6 +496,9 @@ static void dispatch_dots_mc(const CocgArgs<T>& a, int buf, int num_sms, cudaStr
   if constexpr (NC == 2 && MC == 2 && sizeof(T) == 4) {
     if (a.occ >= 3) kern = a.occ >= 4 ? k_cocg_dots_occ<T, MC, 4> : k_cocg_dots_occ<T, MC, 3>;
   }
+  if constexpr (NC == 2 && MC == 4 && sizeof(T) == 4) {
+    if (a.occ >= 2) kern = a.occ >= 3 ? k_cocg_dots_occ<T, MC, 3> : k_cocg_dots_occ<T, MC, 2>;
+  }
   const size_t smem = (size_t)a.lanes * MC * NC * 5 * sizeof(double);
   const int colblocks = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);
   const int64_t groups = (a.n + (int64_t)WARPS * (32 / a.lanes) - 1) / ((int64_t)WARPS * (32 / a.lanes));
@@ -524,6 +527,14 @@ void launch_cocg_reset(const CocgArgs<T>& a, int NC, cudaStream_t s) {
 template <typename T, int NC>
 static void dispatch_dots(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
   constexpr int SC = small_cpl_of<T>(NC), MC = maxcpl_of<T>(NC);
+  // float column pairs: a 4-chunk instance between the 2- and 6-chunk ones,
+  // used when the shape asks for fewer CTAs per SM than its default (occ >= 2)
+  if constexpr (NC == 2 && sizeof(T) == 4) {
+    if (a.occ >= 2 && a.cpl > SC && a.cpl <= 4) {
+      dispatch_dots_mc<T, NC, 4>(a, buf, num_sms, s);
+      return;
+    }
+  }
   if (SC < MC && a.cpl <= SC) dispatch_dots_mc<T, NC, SC>(a, buf, num_sms, s);
   else dispatch_dots_mc<T, NC, MC>(a, buf, num_sms, s);
 }
