@@ -114,7 +114,7 @@ struct DenseWs {
   double* R;      // m x m
   double* Rinv;   // m x m
   double* V;      // m x m
-  double* Vw;     // (m+1)^2
+  double* Vw;     // 6 (m+1)^2: eigensolver work
   double* w;      // m
   double* part;   // gram partials
   int* status;    // 4 ints
@@ -124,7 +124,7 @@ struct DenseWs {
 static DenseWs dense_ws(Handle* h, int m) {
   const size_t mm = (size_t)(m + 1) * (m + 1);
   const int parts = 2 * h->num_sms;
-  char* base = (char*)scratch(h, S_GRAM, sizeof(double) * (5 * mm + 2 * (m + 1) +
+  char* base = (char*)scratch(h, S_GRAM, sizeof(double) * (10 * mm + 2 * (m + 1) +
                                                           (size_t)parts * m * m) + 64);
   DenseWs d;
   double* p = (double*)base;
@@ -132,7 +132,7 @@ static DenseWs dense_ws(Handle* h, int m) {
   d.R = p; p += mm;
   d.Rinv = p; p += mm;
   d.V = p; p += mm;
-  d.Vw = p; p += mm;
+  d.Vw = p; p += 6 * mm;
   d.w = p; p += m + 1;
   d.small = p; p += m + 1;
   d.part = p;

@@ -329,6 +329,7 @@ void chol_inv(double* G, int m, int64_t nrows, double* Rfac, double* Rinv, int* 
               cudaStream_t s);
 // one-CTA cyclic Jacobi: A (m x m, ld m, symmetric) -> eigenvalues ascending
 // in w, eigenvectors (columns) in V (m x m, ld m)
+// (work: 6 (m+1)^2 doubles; mixed-precision Jacobi, see kernels_dense.cu)
 void jacobi_eigh(double* A, int m, double* w, double* V, double* work, cudaStream_t s);
 // res_i = ||AQ_i - theta_i Q_i||^2 (sums, m), FP64
 void col_resid2(const double* Q, const double* AQ, const double* theta, int64_t n, int m,

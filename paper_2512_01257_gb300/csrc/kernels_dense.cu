@@ -450,24 +450,35 @@ void chol_inv(double* G, int m, int64_t nrows, double* Rfac, double* Rinv, int* 
 }
 
 // ---------------------------------------------------------------------------
-// one-CTA cyclic Jacobi (round-robin parallel order)
-constexpr size_t JACOBI_SMEM_MAX = 216 * 1024;  // A and V in shared memory up to me = 116
+// one-CTA cyclic Jacobi (round-robin parallel order), in precision T
 // ---------------------------------------------------------------------------
+constexpr size_t JACOBI_SMEM_MAX = 216 * 1024;  // A and V in shared memory up to this size
+
+// A (m x m, ld m, symmetric part taken) -> eigenvalues ascending in w, the
+// matching eigenvectors as the columns of Vout (m x m, ld m). A pair (p, q)
+// is rotated while |a_pq| > rot_tol sqrt(|a_pp a_qq|); the sweeps end when
+// the off-diagonal mass is below off_tol of the total or a sweep rotated
+// nothing. Vg: global fallback for the eigenvector accumulator (me * me).
+template <typename T>
 __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restrict__ w,
-                         double* __restrict__ Vout, double* __restrict__ Vg, int max_sweeps) {
-  extern __shared__ double A[];  // me * me (+ me * me for V when it fits)
+                         double* __restrict__ Vout, T* __restrict__ Vg, int max_sweeps,
+                         double rot_tol, double off_tol) {
+  extern __shared__ unsigned char jsm[];
+  T* A = reinterpret_cast<T*>(jsm);  // me * me (+ me * me for V when it fits)
   const int me = m + (m & 1);
   // the eigenvector accumulator in shared memory when both fit, else in the
   // global work buffer
-  double* Vw = (2 * (size_t)me * me * sizeof(double) <= JACOBI_SMEM_MAX) ? A + me * me : Vg;
-  __shared__ double cs[64 * 2];  // c, s per pair (me/2 <= 64)
+  T* Vw = (2 * (size_t)me * me * sizeof(T) <= JACOBI_SMEM_MAX) ? A + me * me : Vg;
+  __shared__ T cs[64 * 2];  // c, s per pair (me/2 <= 64)
   __shared__ int pq[64 * 2];
   __shared__ double s_off, s_tot;
   __shared__ int s_order[128];
+  __shared__ int s_rot;
+  const T tiny = sizeof(T) == 4 ? (T)1e-37 : (T)1e-300;
   for (int t = threadIdx.x; t < me * me; t += blockDim.x) {
     const int i = t / me, j = t % me;
-    A[t] = (i < m && j < m) ? 0.5 * (Ain[i * m + j] + Ain[j * m + i]) : 0.0;
-    Vw[t] = (i == j) ? 1.0 : 0.0;
+    A[t] = (i < m && j < m) ? (T)(0.5 * (Ain[i * m + j] + Ain[j * m + i])) : (T)0;
+    Vw[t] = (i == j) ? (T)1 : (T)0;
   }
   __syncthreads();
   const int np = me / 2;
@@ -476,12 +487,13 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
     if (threadIdx.x == 0) {
       s_off = 0.0;
       s_tot = 0.0;
+      s_rot = 0;
     }
     __syncthreads();
     double off = 0.0, tot = 0.0;
     for (int t = threadIdx.x; t < me * me; t += blockDim.x) {
       const int i = t / me, j = t % me;
-      const double a2 = A[t] * A[t];
+      const double a2 = (double)A[t] * (double)A[t];
       tot += a2;
       if (i != j) off += a2;
     }
@@ -492,7 +504,7 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
       atomicAdd(&s_tot, tot);
     }
     __syncthreads();
-    if (!(s_off > 1e-32 * s_tot) || s_tot == 0.0) break;
+    if (!(s_off > off_tol * s_tot) || s_tot == 0.0) break;
     for (int round = 0; round < me - 1; ++round) {
       for (int k = threadIdx.x; k < np; k += blockDim.x) {
         // circle method: position 0 fixed, others rotate
@@ -503,16 +515,16 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
           p = q;
           q = t;
         }
-        const double apq = A[p * me + q];
-        double c = 1.0, s = 0.0;
-        const double app = A[p * me + p], aqq = A[q * me + q];
-        if (apq != 0.0 && fabs(apq) > 1e-300 &&
-            fabs(apq) > 1e-17 * sqrt(fabs(app * aqq))) {
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double at = fabs(tau);
-          const double root = at > 1e150 ? at : sqrt(1.0 + tau * tau);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (at + root);
-          c = 1.0 / sqrt(1.0 + t * t);
+        const T apq = A[p * me + q];
+        T c = (T)1, s = (T)0;
+        const T app = A[p * me + p], aqq = A[q * me + q];
+        if (apq != (T)0 && fabs(apq) > tiny && fabs(apq) > (T)rot_tol * sqrt(fabs(app * aqq))) {
+          s_rot = 1;
+          const T tau = (aqq - app) / ((T)2 * apq);
+          const T at = fabs(tau);
+          const T root = at > (T)1e15 ? at : sqrt((T)1 + tau * tau);
+          const T t = (tau >= (T)0 ? (T)1 : (T)-1) / (at + root);
+          c = (T)1 / sqrt((T)1 + t * t);
           s = t * c;
         }
         cs[2 * k] = c;
@@ -527,41 +539,43 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
       // rotated diagonal blocks lose their off-diagonal entry
       for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
         const int j = t / np, k = t % np;
-        const double cj = cs[2 * j], sj = cs[2 * j + 1];
-        const double ck = cs[2 * k], sk = cs[2 * k + 1];
-        if (sj == 0.0 && sk == 0.0) continue;
+        const T cj = cs[2 * j], sj = cs[2 * j + 1];
+        const T ck = cs[2 * k], sk = cs[2 * k + 1];
+        if (sj == (T)0 && sk == (T)0) continue;
         const int pj = pq[2 * j], qj = pq[2 * j + 1];
         const int pk = pq[2 * k], qk = pq[2 * k + 1];
-        const double a11 = A[pj * me + pk], a12 = A[pj * me + qk];
-        const double a21 = A[qj * me + pk], a22 = A[qj * me + qk];
+        const T a11 = A[pj * me + pk], a12 = A[pj * me + qk];
+        const T a21 = A[qj * me + pk], a22 = A[qj * me + qk];
         // rows: L_j B
-        const double b11 = cj * a11 - sj * a21, b12 = cj * a12 - sj * a22;
-        const double b21 = sj * a11 + cj * a21, b22 = sj * a12 + cj * a22;
+        const T b11 = cj * a11 - sj * a21, b12 = cj * a12 - sj * a22;
+        const T b21 = sj * a11 + cj * a21, b22 = sj * a12 + cj * a22;
         // columns: (L_j B) R_k
         A[pj * me + pk] = ck * b11 - sk * b12;
-        A[pj * me + qk] = j == k ? 0.0 : sk * b11 + ck * b12;
-        A[qj * me + pk] = j == k ? 0.0 : ck * b21 - sk * b22;
+        A[pj * me + qk] = j == k ? (T)0 : sk * b11 + ck * b12;
+        A[qj * me + pk] = j == k ? (T)0 : ck * b21 - sk * b22;
         A[qj * me + qk] = sk * b21 + ck * b22;
       }
       // V R_k
       for (int t = threadIdx.x; t < np * me; t += blockDim.x) {
         const int k = t / me, row = t % me;
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        if (s == 0.0) continue;
+        const T c = cs[2 * k], s = cs[2 * k + 1];
+        if (s == (T)0) continue;
         const int p = pq[2 * k], q = pq[2 * k + 1];
-        const double vp = Vw[row * me + p], vq = Vw[row * me + q];
+        const T vp = Vw[row * me + p], vq = Vw[row * me + q];
         Vw[row * me + p] = c * vp - s * vq;
         Vw[row * me + q] = s * vp + c * vq;
       }
       __syncthreads();
     }
+    if (s_rot == 0) break;  // nothing was above the threshold in this sweep
+    __syncthreads();
   }
   // sort eigenvalues ascending (m <= 128), then write w and V columns
   if (threadIdx.x == 0) {
     for (int i = 0; i < m; ++i) s_order[i] = i;
     for (int i = 1; i < m; ++i) {
       const int key = s_order[i];
-      const double kv = A[key * me + key];
+      const T kv = A[key * me + key];
       int j = i - 1;
       while (j >= 0 && A[s_order[j] * me + s_order[j]] > kv) {
         s_order[j + 1] = s_order[j];
@@ -571,21 +585,74 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = A[s_order[i] * me + s_order[i]];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = (double)A[s_order[i] * me + s_order[i]];
   for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
     const int r = t / m, c = t % m;
-    Vout[r * m + c] = Vw[r * me + s_order[c]];
+    Vout[r * m + c] = (double)Vw[r * me + s_order[c]];
   }
 }
 
+// small dense product, all m x m row-major: C = alpha op(A) op(B) + gamma I,
+// op = transpose when the flag is set; one thread per entry of C
+__global__ void k_small_gemm(const double* __restrict__ A, int ta, const double* __restrict__ B,
+                             int tb, double* __restrict__ C, int m, double alpha, double gamma) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  const int i = e / m, j = e - (e / m) * m;
+  double acc = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const double a = ta ? A[k * m + i] : A[i * m + k];
+    const double b = tb ? B[j * m + k] : B[k * m + j];
+    acc = fma(a, b, acc);
+  }
+  C[e] = alpha * acc + (i == j ? gamma : 0.0);
+}
+
+static void small_gemm(const double* A, int ta, const double* B, int tb, double* C, int m,
+                       double alpha, double gamma, cudaStream_t s) {
+  k_small_gemm<<<(m * m + 127) / 128, 128, 0, s>>>(A, ta, B, tb, C, m, alpha, gamma);
+  RF_LAUNCH();
+}
+
+template <typename T>
+static void jacobi_launch(const double* A, int m, double* w, double* V, T* Vg, int sweeps,
+                          double rot_tol, double off_tol, cudaStream_t s) {
+  const int me = m + (m & 1);
+  size_t smem = (size_t)me * me * sizeof(T);
+  if (2 * smem <= JACOBI_SMEM_MAX) smem *= 2;  // V beside A
+  ensure_dyn_smem(reinterpret_cast<const void*>(k_jacobi<T>), smem);
+  k_jacobi<T><<<1, 512, smem, s>>>(A, m, w, V, Vg, sweeps, rot_tol, off_tol);
+  RF_LAUNCH();
+}
+
+// Mixed-precision Jacobi. GB300's FP64 rate is a small fraction of its FP32
+// rate, and a one-CTA Jacobi on an 80 x 80 matrix is bound by one SM's FP64
+// issue. So: (1) float Jacobi to the float rounding floor gives V1 with
+// V1^T A V1 diagonal to ~1e-7; (2) two Newton-Schulz steps
+// V <- V (3 I - V^T V) / 2 make V1 orthonormal to working precision (its
+// float error is ~1e-6, each step squares it); (3) the FP64 Jacobi on
+// B = V^T A V, already nearly diagonal, needs a few sweeps; (4) V = V1 V_B.
+// The final accuracy is that of the FP64 Jacobi, as with FP64 alone.
 void jacobi_eigh(double* A, int m, double* w, double* V, double* work, cudaStream_t s) {
   if (m > 128) throw Err{RAFEAST_ERR_INVALID_ARG};
   const int me = m + (m & 1);
-  size_t smem = (size_t)me * me * sizeof(double);
-  if (2 * smem <= JACOBI_SMEM_MAX) smem *= 2;  // V beside A
-  ensure_dyn_smem(reinterpret_cast<const void*>(k_jacobi), smem);
-  k_jacobi<<<1, 512, smem, s>>>(A, m, w, V, work, 40);
-  RF_LAUNCH();
+  const size_t mm = (size_t)me * me;
+  double* W1 = work;
+  double* W2 = work + mm;
+  double* S = work + 2 * mm;
+  double* B = work + 3 * mm;
+  double* VB = work + 4 * mm;
+  double* Vg = work + 5 * mm;  // also the float stage's fallback accumulator
+  jacobi_launch<float>(A, m, w, W1, reinterpret_cast<float*>(Vg), 30, 1e-6, 1e-13, s);
+  for (int it = 0; it < 2; ++it) {
+    small_gemm(W1, 1, W1, 0, S, m, -0.5, 1.5, s);  // S = (3 I - V^T V) / 2
+    small_gemm(W1, 0, S, 0, W2, m, 1.0, 0.0, s);   // V <- V S
+    std::swap(W1, W2);
+  }
+  small_gemm(A, 0, W1, 0, S, m, 1.0, 0.0, s);  // A V
+  small_gemm(W1, 1, S, 0, B, m, 1.0, 0.0, s);  // V^T A V
+  jacobi_launch<double>(B, m, w, VB, Vg, 40, 1e-17, 1e-32, s);
+  small_gemm(W1, 0, VB, 0, V, m, 1.0, 0.0, s);  // V1 V_B
 }
 
 // ---------------------------------------------------------------------------
