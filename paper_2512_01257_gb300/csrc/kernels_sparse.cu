@@ -496,7 +496,7 @@ static void dispatch_dots_mc(const CocgArgs<T>& a, int buf, int num_sms, cudaStr
   if constexpr (NC == 2 && MC == 2 && sizeof(T) == 4) {
     if (a.occ >= 3) kern = a.occ >= 4 ? k_cocg_dots_occ<T, MC, 4> : k_cocg_dots_occ<T, MC, 3>;
   }
-  if constexpr (NC == 2 && MC == 4 && sizeof(T) == 4) {
+  if constexpr (NC == 2 && (MC == 3 || MC == 4) && sizeof(T) == 4) {
     if (a.occ >= 2) kern = a.occ >= 3 ? k_cocg_dots_occ<T, MC, 3> : k_cocg_dots_occ<T, MC, 2>;
   }
   const size_t smem = (size_t)a.lanes * MC * NC * 5 * sizeof(double);
@@ -527,11 +527,12 @@ void launch_cocg_reset(const CocgArgs<T>& a, int NC, cudaStream_t s) {
 template <typename T, int NC>
 static void dispatch_dots(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
   constexpr int SC = small_cpl_of<T>(NC), MC = maxcpl_of<T>(NC);
-  // float column pairs: a 4-chunk instance between the 2- and 6-chunk ones,
+  // float column pairs: 3- and 4-chunk instances between the 2- and 6-chunk ones,
   // used when the shape asks for fewer CTAs per SM than its default (occ >= 2)
   if constexpr (NC == 2 && sizeof(T) == 4) {
     if (a.occ >= 2 && a.cpl > SC && a.cpl <= 4) {
-      dispatch_dots_mc<T, NC, 4>(a, buf, num_sms, s);
+      if (a.cpl == 3) dispatch_dots_mc<T, NC, 3>(a, buf, num_sms, s);
+      else dispatch_dots_mc<T, NC, 4>(a, buf, num_sms, s);
       return;
     }
   }
