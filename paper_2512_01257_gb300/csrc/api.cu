@@ -202,6 +202,51 @@ static void rayleigh_ritz_dev(Handle* h, const double* X, int m, int ld, double*
   h->spmm_launches += 2;
 }
 
+// Cholesky-QR2 and Rayleigh-Ritz with the last factor folded in (the outer
+// loop's orthonormalise + Rayleigh-Ritz): the passes before the last form
+// X <- X R^{-1}; the last pass's R^{-1} is not applied. With Z = X R^{-1}:
+// Z^T A Z = R^{-T} (X^T A X) R^{-1} = V diag(theta) V^T, and the Ritz vectors
+// are Z V = X (R^{-1} V), one tall product instead of two. Qout = X (R^{-1} V),
+// AQout = A Qout. ev_mid is recorded between the factorisations and the rest.
+// Returns the number of shifted passes.
+static int cholqr_rr(Handle* h, double*& X, double*& tmp, double* tmp2, int m, int ld,
+                     double* Qout, double* AQout, double* theta_d, cudaEvent_t ev_mid) {
+  DenseWs d = dense_ws(h, m);
+  int shifted = 0;
+  int passes = 2;
+  for (int pass = 0; pass < passes; ++pass) {
+    gram(X, X, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true);
+    chol_inv(d.G, m, h->n, d.R, d.Rinv, d.status, h->stream);
+    h->launches += 3;
+    int st = 0;
+    RF_CUDA(cudaMemcpyAsync(&st, d.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    if (st == 2) throw Err{RAFEAST_ERR_CHOLESKY};
+    if (st == 1) {
+      ++shifted;
+      if (passes < 4) ++passes;
+    }
+    if (pass == passes - 1) break;  // the last factor is folded into Rayleigh-Ritz
+    tall_gemm(X, h->n, m, ld, d.Rinv, m, tmp, ld, h->stream, true);
+    h->launches += 1;
+    std::swap(X, tmp);
+  }
+  RF_CUDA(cudaEventRecord(ev_mid, h->stream));
+  launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m, ld, 1.0, h->shift, X, tmp2,
+                           h->num_sms, h->stream);
+  gram(X, tmp2, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true);  // X^T A X
+  small_gemm(d.G, 0, d.Rinv, 0, d.R, m, 1.0, 0.0, h->stream);            // (X^T A X) R^-1
+  small_gemm(d.Rinv, 1, d.R, 0, d.G, m, 1.0, 0.0, h->stream);            // R^-T (.)
+  jacobi_eigh(d.G, m, theta_d, d.V, d.Vw, h->stream);
+  small_gemm(d.Rinv, 0, d.V, 0, d.R, m, 1.0, 0.0, h->stream);  // R^-1 V
+  tall_gemm(X, h->n, m, ld, d.R, m, Qout, ld, h->stream);
+  launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m, ld, 1.0, h->shift, Qout,
+                           AQout, h->num_sms, h->stream);
+  h->launches += 9;
+  h->spmm_launches += 2;
+  return shifted;
+}
+
 static void residuals_host(Handle* h, const double* Q, const double* AQ, const double* theta_d,
                            int m, int ld, std::vector<double>& res) {
   DenseWs d = dense_ws(h, m);
@@ -1242,9 +1287,7 @@ static bool solve_outer_tail(SolveRun& r) {
   const int m0 = r.m0, ldq = r.ldq;
   double* X = r.Qt;
   double* Y = r.T1;
-  r.shifted_total += cholqr(h, X, Y, m0, ldq, nullptr);
-  RF_CUDA(cudaEventRecord(r.ev[4], h->stream));
-  rayleigh_ritz_dev(h, X, m0, ldq, h->Q, h->AQ, h->theta_d, r.T2);
+  r.shifted_total += cholqr_rr(h, X, Y, r.T2, m0, ldq, h->Q, h->AQ, h->theta_d, r.ev[4]);
   residuals_host(h, h->Q, h->AQ, h->theta_d, m0, ldq, r.res);
   RF_CUDA(cudaEventRecord(r.ev[5], h->stream));
   h->theta.resize(m0);

@@ -330,6 +330,10 @@ void chol_inv(double* G, int m, int64_t nrows, double* Rfac, double* Rinv, int* 
 // one-CTA cyclic Jacobi: A (m x m, ld m, symmetric) -> eigenvalues ascending
 // in w, eigenvectors (columns) in V (m x m, ld m)
 // (work: 6 (m+1)^2 doubles; mixed-precision Jacobi, see kernels_dense.cu)
+// m x m row-major C = alpha op(A) op(B) + gamma I (ta, tb: transpose); C must
+// not alias A or B
+void small_gemm(const double* A, int ta, const double* B, int tb, double* C, int m, double alpha,
+                double gamma, cudaStream_t s);
 void jacobi_eigh(double* A, int m, double* w, double* V, double* work, cudaStream_t s);
 // res_i = ||AQ_i - theta_i Q_i||^2 (sums, m), FP64
 void col_resid2(const double* Q, const double* AQ, const double* theta, int64_t n, int m,

@@ -608,8 +608,8 @@ __global__ void k_small_gemm(const double* __restrict__ A, int ta, const double*
   C[e] = alpha * acc + (i == j ? gamma : 0.0);
 }
 
-static void small_gemm(const double* A, int ta, const double* B, int tb, double* C, int m,
-                       double alpha, double gamma, cudaStream_t s) {
+void small_gemm(const double* A, int ta, const double* B, int tb, double* C, int m, double alpha,
+                double gamma, cudaStream_t s) {
   k_small_gemm<<<(m * m + 127) / 128, 128, 0, s>>>(A, ta, B, tb, C, m, alpha, gamma);
   RF_LAUNCH();
 }
