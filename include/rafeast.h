@@ -104,6 +104,13 @@ extern "C" {
                                      * M p_k follows by its recurrence; no    *
                                      * gathers in the update). Batched solves *
                                      * follow the first handle's setting.     */
+#define RAFEAST_OPT_VALUES_FREE 13  /* 0 (default): when the CSR part of A  *
+                                     * is a unit-weight graph Laplacian (off- *
+                                     * diagonal values -1, diagonal = degree) *
+                                     * the multi-shift dot kernels gather on  *
+                                     * its off-diagonal pattern alone, with   *
+                                     * L r = deg r - sum of neighbours; 1:    *
+                                     * always read the values                 */
 #define RAFEAST_OPT_TEST_STALL 9    /* test hook: bytes (multiple of 16) that  *
                                      * every bulk-copy stage waits for and no *
                                      * copy delivers, so the bounded wait     *

@@ -633,6 +633,10 @@ static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double*
   a.sst = (ShiftState*)(sc + o_sst);
   a.scf = (ShiftCoef<T>*)(sc + o_scf);
   if (ctl_dev) a.ctl = ctl_dev;
+  if (h->lcolidx && h->opt_values_free == 0) {
+    a.lrowptr = h->lrowptr;
+    a.lcolidx = h->lcolidx;
+  }
   launch_ms_init<T>(a, m0, h->num_sms, st);
   h->launches += 2;
   MsProblem<T> P;
@@ -650,9 +654,12 @@ static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double*
 // the seed r and p, the shifted directions and the quadrature sum
 // (streamed update: the dot kernel also writes w; the update kernel reads
 // r, p, w, s and writes r, p, s, and reads no A)
-static double ms_dots_bytes(const Handle* h, int act_d, bool fp64, bool stream = false) {
+static double ms_dots_bytes(const Handle* h, int act_d, bool fp64, bool stream = false,
+                            bool vf = false) {
   const double sv = fp64 ? 8.0 : 4.0;
-  const double abytes = (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
+  // values-free gathers read the off-diagonal pattern only
+  const double abytes = vf ? (double)h->nnz_off * 4.0 + 4.0 * (h->n + 1)
+                           : (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
   const double pairb = (double)h->n * 2 * 2.0 * sv;
   return abytes + pairb * act_d * (stream ? 2.0 : 1.0);
 }
@@ -842,7 +849,7 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
       const int act_u = hist[k];
       h->prof[0] += 1;
       h->prof[1] += tk[2 * k];
-      h->prof[2] += ms_dots_bytes(h, act_d, fp64, stream);
+      h->prof[2] += ms_dots_bytes(h, act_d, fp64, stream, a.lcolidx != nullptr);
       if (act_u > 0) {
         h->prof[3] += 1;
         h->prof[4] += tk[2 * k + 1];
@@ -917,10 +924,16 @@ static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cud
   gd.gg_u = (const int4*)(bb + o_ggu);
   // (lanes, chunks) of a kernel: 0 = each problem's own default (at most two
   // chunks per lane, the two-CTA-per-SM instances), else one shape for all
+  bool all_vf = true;
+  for (int t = 0; t < cnt; ++t) all_vf = all_vf && P[t].a.lcolidx != nullptr;
   auto shaped = [&](int G, int cpl) {
     std::vector<CocgArgs<T>> v(cnt);
     for (int t = 0; t < cnt; ++t) {
       v[t] = P[t].a;
+      if (!all_vf) {  // values-free gathers only when every problem has them
+        v[t].lrowptr = nullptr;
+        v[t].lcolidx = nullptr;
+      }
       if (G == 0) {
         int cb = 1;
         choose_shape(P[t].pairs, 2, fp64, 0, v[t].lanes, v[t].cpl, cb,
@@ -1082,7 +1095,7 @@ static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cud
         const int act_d = k == 0 ? P[t].pairs : hist[t][k - 1];
         const int act_u = hist[t][k];
         const bool st = P[t].a.wbuf != nullptr;
-        bd += ms_dots_bytes(items[t]->h, act_d, fp64, st);
+        bd += ms_dots_bytes(items[t]->h, act_d, fp64, st, all_vf);
         if (act_u > 0) bu += ms_update_bytes(items[t]->h, act_u, P[t].ns, fp64, st);
         if (act_d > 0) ++probs;
         pairs_act += act_d;
@@ -1541,6 +1554,43 @@ int rafeast_create(rafeast_t* out, int64_t n, int64_t nnz, const int32_t* row_pt
       RF_CUDA(cudaMemcpy(h->iperm, ip.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
     }
     h->reordered = reorder;
+    // a unit-weight graph Laplacian (every off-diagonal value -1, one diagonal
+    // entry per row equal to the row's off-diagonal count) also gets its
+    // off-diagonal pattern, for the values-free gathers
+    bool unit = nnz > 0;
+    for (int64_t r = 0; r < n && unit; ++r) {
+      int deg = 0, ndiag = 0;
+      double dv = 0.0;
+      for (int32_t k = rp2[r]; k < rp2[r + 1]; ++k) {
+        if (ci2[k] == r) {
+          ++ndiag;
+          dv = va2[k];
+        } else if (va2[k] == -1.0) {
+          ++deg;
+        } else {
+          unit = false;
+        }
+      }
+      if (ndiag > 1 || dv != (double)deg) unit = false;
+    }
+    if (unit) {
+      std::vector<int32_t> lrp(n + 1), lci;
+      lci.reserve(nnz);
+      lrp[0] = 0;
+      for (int64_t r = 0; r < n; ++r) {
+        for (int32_t k = rp2[r]; k < rp2[r + 1]; ++k)
+          if (ci2[k] != r) lci.push_back(ci2[k]);
+        lrp[r + 1] = (int32_t)lci.size();
+      }
+      h->nnz_off = (int64_t)lci.size();
+      RF_CUDA(cudaMalloc(&h->lrowptr, sizeof(int32_t) * (n + 1)));
+      RF_CUDA(cudaMalloc(&h->lcolidx, sizeof(int32_t) * std::max<int64_t>(h->nnz_off, 1)));
+      RF_CUDA(cudaMemcpy(h->lrowptr, lrp.data(), sizeof(int32_t) * (n + 1),
+                         cudaMemcpyHostToDevice));
+      if (h->nnz_off)
+        RF_CUDA(cudaMemcpy(h->lcolidx, lci.data(), sizeof(int32_t) * h->nnz_off,
+                           cudaMemcpyHostToDevice));
+    }
     std::vector<float> v32(nnz);
     for (int64_t k = 0; k < nnz; ++k) v32[k] = (float)va2[k];
     RF_CUDA(cudaMalloc(&h->rowptr, sizeof(int32_t) * (n + 1)));
@@ -1572,8 +1622,8 @@ void rafeast_destroy(rafeast_t hh) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& b : h->bufs)
     if (b.p) cudaFree(b.p);
-  void* ptrs[] = {h->rowptr, h->colidx, h->val64, h->val32, h->perm, h->iperm,
-                  h->Q,      h->AQ,     h->theta_d};
+  void* ptrs[] = {h->rowptr, h->colidx, h->val64,   h->val32,  h->perm,   h->iperm,
+                  h->Q,      h->AQ,     h->theta_d, h->lrowptr, h->lcolidx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -1620,6 +1670,10 @@ int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
     case RAFEAST_OPT_UPDATE:
       if (value < 0 || value > 2) return RAFEAST_ERR_INVALID_ARG;
       h->opt_update = (int)value;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_VALUES_FREE:
+      if (value < 0 || value > 1) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_values_free = (int)value;
       return RAFEAST_OK;
     case RAFEAST_OPT_CPL:
       if (value < 0 || value > 16) return RAFEAST_ERR_INVALID_ARG;

@@ -88,6 +88,46 @@ __device__ __forceinline__ void gather_row(const int32_t* __restrict__ colidx,
   }
 }
 
+// values-free gather for a unit-weight Laplacian's off-diagonal pattern:
+// acc[c][j] += sum_k X[col_k][chunk c] (weights all +1; the -1 sign and the
+// degree term are applied by the caller). Two entries in flight per step, a
+// missing second entry re-reads the first row with weight zero.
+template <typename T, int NC, int MAXCPL>
+__device__ __forceinline__ void gather_row_vf(const int32_t* __restrict__ colidx, int k0, int k1,
+                                              int row, int lg, int G, unsigned gmask,
+                                              const T* __restrict__ X, int64_t ldx_t,
+                                              const int (&coff)[MAXCPL], unsigned mask,
+                                              c2<T> (&acc)[MAXCPL][NC]) {
+  using C = c2<T>;
+  for (int kb = k0; kb < k1; kb += G) {
+    const int kk = kb + lg;
+    const int my_c = kk < k1 ? __ldg(colidx + kk) : row;
+    const int cnt = min(G, k1 - kb);
+    for (int e = 0; e < cnt; e += 2) {
+      const int ca = __shfl_sync(gmask, my_c, e, G);
+      const int cb = __shfl_sync(gmask, my_c, e + 1 < cnt ? e + 1 : e, G);
+      const T vb = e + 1 < cnt ? (T)1 : (T)0;
+      C xa[MAXCPL][NC], xb[MAXCPL][NC];
+#pragma unroll
+      for (int c = 0; c < MAXCPL; ++c)
+        if (mask & (1u << c)) {
+          ld_chunk<NC>(X + (int64_t)ca * ldx_t + coff[c], xa[c]);
+          ld_chunk<NC>(X + (int64_t)cb * ldx_t + coff[c], xb[c]);
+        }
+#pragma unroll
+      for (int c = 0; c < MAXCPL; ++c)
+        if (mask & (1u << c)) {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) {
+            acc[c][j].x += xa[c][j].x;
+            acc[c][j].y += xa[c][j].y;
+            acc[c][j] = crfma<T>(vb, xb[c][j], acc[c][j]);
+          }
+        }
+    }
+  }
+}
+
 // two arrays at once (update kernel): acc_r from R, acc_p from P
 template <typename T, int NC, int MAXCPL>
 __device__ __forceinline__ void gather_row2(const int32_t* __restrict__ colidx,
@@ -162,7 +202,7 @@ __device__ __forceinline__ RowMap row_map(int G, int cpl, const Blk& b) {
 // delta = r^T w, nu = ||r||^2 reduced into a.acc; the last CTA of the
 // problem (ticket over blk.gx * blk.gy CTAs) runs the scalar step on *src.
 // ---------------------------------------------------------------------------
-template <typename T, int NC, int MAXCPL>
+template <typename T, int NC, int MAXCPL, bool VF = false>
 __device__ __forceinline__ void cocg_dots_body(const CocgArgs<T>& a, const CocgArgs<T>* src, int buf,
     const Blk& blk) {
   using C = c2<T>;
@@ -194,15 +234,22 @@ __device__ __forceinline__ void cocg_dots_body(const CocgArgs<T>& a, const CocgA
   // every lane of a group must run the row loop (its shuffles name the whole
   // group); lanes without a chunk take part but load nothing
   if (__any_sync(0xffffffffu, mask != 0)) {
+    const int32_t* __restrict__ rowptr = VF ? a.lrowptr : a.rowptr;
     for (int64_t row = mp.gid; row < a.n; row += mp.gstride) {
-      const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
+      const int k0 = __ldg(rowptr + row), k1 = __ldg(rowptr + row + 1);
       C acc[MAXCPL][NC];
 #pragma unroll
       for (int c = 0; c < MAXCPL; ++c)
 #pragma unroll
         for (int j = 0; j < NC; ++j) acc[c][j] = mk<T>((T)0, (T)0);
-      gather_row<T, NC, MAXCPL>(a.colidx, a.val, k0, k1, (int)row, mp.lg, mp.G, gmask, R, ldt,
-                                coff, mask, acc);
+      if constexpr (VF)
+        gather_row_vf<T, NC, MAXCPL>(a.lcolidx, k0, k1, (int)row, mp.lg, mp.G, gmask, R, ldt,
+                                     coff, mask, acc);
+      else
+        gather_row<T, NC, MAXCPL>(a.colidx, a.val, k0, k1, (int)row, mp.lg, mp.G, gmask, R, ldt,
+                                  coff, mask, acc);
+      // values-free: L r = deg r - (sum over neighbours), deg = k1 - k0
+      const T deg = (T)(k1 - k0);
 #pragma unroll
       for (int c = 0; c < MAXCPL; ++c)
         if (mask & (1u << c)) {
@@ -210,7 +257,9 @@ __device__ __forceinline__ void cocg_dots_body(const CocgArgs<T>& a, const CocgA
           ld_chunk<NC>(R + row * ldt + coff[c], rv);
 #pragma unroll
           for (int j = 0; j < NC; ++j) {
-            const C w = csub<T>(cmul<T>(zv[j], rv[j]), acc[c][j]);
+            const C lr = VF ? mk<T>(deg * rv[j].x - acc[c][j].x, deg * rv[j].y - acc[c][j].y)
+                            : acc[c][j];
+            const C w = csub<T>(cmul<T>(zv[j], rv[j]), lr);
             wv[j] = w;
             // gamma += r r, delta += r w, nu += |r|^2
             dg_re[c][j] = fma(rv[j].x, rv[j].x, fma(-rv[j].y, rv[j].y, dg_re[c][j]));

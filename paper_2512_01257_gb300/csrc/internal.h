@@ -137,6 +137,11 @@ template <typename T> struct CocgArgs {
   // place (r[0] == r[1], p[0] == p[1]), s is kept in sbuf
   T* wbuf;
   T* sbuf;
+  // values-free Laplacian gathers (lcolidx != null): A = L + shift I with L a
+  // unit-weight graph Laplacian (off-diagonal -1, diagonal = degree); lrowptr
+  // and lcolidx hold the off-diagonal pattern only, L r = deg r - sum r_nbr
+  const int32_t* lrowptr;
+  const int32_t* lcolidx;
 };
 
 // ---- handle -----------------------------------------------------------------
@@ -157,6 +162,10 @@ struct Handle {
   int32_t* colidx = nullptr;
   double* val64 = nullptr;
   float* val32 = nullptr;
+  // the off-diagonal pattern when A's CSR part is a unit-weight Laplacian
+  int32_t* lrowptr = nullptr;
+  int32_t* lcolidx = nullptr;
+  int64_t nnz_off = 0;
   double shift = 0.0;
   double norm1 = 0.0, glo = 0.0, ghi = 0.0;
   bool reordered = false;
@@ -176,6 +185,7 @@ struct Handle {
   int opt_cpl = 0;     // cap on column chunks per lane (0: kernel maximum)
   int opt_solver = 1;  // 0: COCG per shift, 1: multi-shift COCG (default)
   int opt_update = 0;  // multi-shift update: 0 auto, 1 gathered products, 2 streamed
+  int opt_values_free = 0;  // 0: values-free gathers for unit Laplacians, 1: never
   // autotuned kernel shapes (lanes, chunks per lane) of the multi-shift
   // kernels, keyed by (pairs, shifts, precision)
   struct Shape {

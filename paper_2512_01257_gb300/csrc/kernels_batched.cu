@@ -180,7 +180,7 @@ __device__ __forceinline__ int next_item(unsigned int* counter, int total) {
   return s_item;
 }
 
-template <typename T, int MAXCPL>
+template <typename T, int MAXCPL, bool VF>
 __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && MAXCPL * 2 <= 4) ? 2 : 1)
     k_ms_dots_grouped(const CocgArgs<T>* __restrict__ args, int* __restrict__ map_d,
                       int* __restrict__ map_u, GroupCtl* __restrict__ gc,
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && MAXCPL * 2 <= 4) ?
     if (item < 0) break;
     const int t = item_owner(m, count, item);
     const CocgArgs<T> a = args[t];
-    cocg_dots_body<T, 2, MAXCPL>(a, args + t, buf, item_blk(m, count, t, item));
+    cocg_dots_body<T, 2, MAXCPL, VF>(a, args + t, buf, item_blk(m, count, t, item));
   }
   // every CTA takes a global ticket once the queue is empty; all items (and
   // every problem's scalar step) are then done, and the last CTA re-plans
@@ -302,9 +302,13 @@ static const void* stream_fn(int ns) {
 }
 
 template <typename T>
-static const void* dots_fn(int mc) {
-  if (mc <= 2) return reinterpret_cast<const void*>(k_ms_dots_grouped<T, 2>);
-  return reinterpret_cast<const void*>(k_ms_dots_grouped<T, grouped_mc_large<T>()>);
+static const void* dots_fn(int mc, bool vf) {
+  if (vf) {
+    if (mc <= 2) return reinterpret_cast<const void*>(k_ms_dots_grouped<T, 2, true>);
+    return reinterpret_cast<const void*>(k_ms_dots_grouped<T, grouped_mc_large<T>(), true>);
+  }
+  if (mc <= 2) return reinterpret_cast<const void*>(k_ms_dots_grouped<T, 2, false>);
+  return reinterpret_cast<const void*>(k_ms_dots_grouped<T, grouped_mc_large<T>(), false>);
 }
 
 template <typename T>
@@ -382,7 +386,12 @@ void plan_ms_grouped(const std::vector<CocgArgs<T>>& args_d, const std::vector<C
   g.mc_d = cd <= 2 ? 2 : grouped_mc_large<T>();
   g.mc_u = cu <= 2 ? 2 : grouped_mc_large<T>();
   g.smem_dots = (size_t)ld * g.mc_d * 2 * 5 * sizeof(double);
-  g.fn_dots = dots_fn<T>(g.mc_d);
+  // values-free dot instances when the problems carry the off-diagonal
+  // pattern of a unit-weight Laplacian (all of them or none)
+  const bool vf = args_d[0].lcolidx != nullptr;
+  for (int t = 0; t < cnt; ++t)
+    RF_CHECK((args_d[t].lcolidx != nullptr) == vf, RAFEAST_ERR_INVALID_ARG);
+  g.fn_dots = dots_fn<T>(g.mc_d, vf);
   if (stream) {
     g.smem_upd = ms_stream_smem<T>(pmax, g.ns);
     g.fn_upd = stream_fn<T>(g.ns);

@@ -120,10 +120,10 @@ __global__ void __launch_bounds__(THREADS) k_cocg_init(CocgArgs<T> a) {
 // ---------------------------------------------------------------------------
 // COCG dots kernel
 // ---------------------------------------------------------------------------
-template <typename T, int NC, int MAXCPL>
+template <typename T, int NC, int MAXCPL, bool VF = false>
 __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && MAXCPL * NC <= 4) ? 2 : 1)
     k_cocg_dots(CocgArgs<T> a, int buf) {
-  cocg_dots_body<T, NC, MAXCPL>(a, &a, buf, grid_blk());
+  cocg_dots_body<T, NC, MAXCPL, VF>(a, &a, buf, grid_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -289,9 +289,9 @@ template <typename T, int NS, int MAXCPL, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_ms_update_occ(CocgArgs<T> a, int buf) {
   ms_update_body<T, NS, MAXCPL>(a, &a, buf, grid_blk());
 }
-template <typename T, int MAXCPL, int MINB>
+template <typename T, int MAXCPL, int MINB, bool VF = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_cocg_dots_occ(CocgArgs<T> a, int buf) {
-  cocg_dots_body<T, 2, MAXCPL>(a, &a, buf, grid_blk());
+  cocg_dots_body<T, 2, MAXCPL, VF>(a, &a, buf, grid_blk());
 }
 
 template <typename T, int NS>
@@ -493,11 +493,21 @@ __global__ void __launch_bounds__(THREADS) k_spmm_real(int64_t n, const int32_t*
 template <typename T, int NC, int MC>
 static void dispatch_dots_mc(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
   auto kern = k_cocg_dots<T, NC, MC>;
-  if constexpr (NC == 2 && MC == 2 && sizeof(T) == 4) {
-    if (a.occ >= 3) kern = a.occ >= 4 ? k_cocg_dots_occ<T, MC, 4> : k_cocg_dots_occ<T, MC, 3>;
-  }
-  if constexpr (NC == 2 && (MC == 3 || MC == 4) && sizeof(T) == 4) {
-    if (a.occ >= 2) kern = a.occ >= 3 ? k_cocg_dots_occ<T, MC, 3> : k_cocg_dots_occ<T, MC, 2>;
+  if constexpr (NC == 2) {
+    // column pairs of the multi-shift seed: values-free instances for a
+    // unit-weight Laplacian (a.lcolidx), occupancy-forced ones (a.occ)
+    const bool vf = a.lcolidx != nullptr;
+    if (vf) kern = k_cocg_dots<T, NC, MC, true>;
+    if constexpr (MC == 2 && sizeof(T) == 4) {
+      if (a.occ >= 3)
+        kern = a.occ >= 4 ? (vf ? k_cocg_dots_occ<T, MC, 4, true> : k_cocg_dots_occ<T, MC, 4>)
+                          : (vf ? k_cocg_dots_occ<T, MC, 3, true> : k_cocg_dots_occ<T, MC, 3>);
+    }
+    if constexpr ((MC == 3 || MC == 4) && sizeof(T) == 4) {
+      if (a.occ >= 2)
+        kern = a.occ >= 3 ? (vf ? k_cocg_dots_occ<T, MC, 3, true> : k_cocg_dots_occ<T, MC, 3>)
+                          : (vf ? k_cocg_dots_occ<T, MC, 2, true> : k_cocg_dots_occ<T, MC, 2>);
+    }
   }
   const size_t smem = (size_t)a.lanes * MC * NC * 5 * sizeof(double);
   const int colblocks = (a.m0 + a.lanes * a.cpl - 1) / (a.lanes * a.cpl);

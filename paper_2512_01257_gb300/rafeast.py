@@ -52,6 +52,7 @@ RAFEAST_OPT_TEST_STALL = 9
 RAFEAST_OPT_CPL = 10
 RAFEAST_OPT_SOLVER = 11
 RAFEAST_OPT_UPDATE = 12
+RAFEAST_OPT_VALUES_FREE = 13
 
 EXPORTS = [
     "rafeast_create", "rafeast_destroy", "rafeast_status_string", "rafeast_set_option",

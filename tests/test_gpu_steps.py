@@ -245,6 +245,65 @@ def test_filter_mixed(lib, form, nc, solver):
         lib.rafeast_destroy(h)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_values_free_gathers(lib, prec):
+    """A unit-weight Laplacian (off-diagonal -1, diagonal = degree; empty rows
+    allowed) is detected at create time and its multi-shift dot kernel
+    gathers on the off-diagonal pattern alone. The filter agrees with the
+    values-reading kernel and with the oracle. A matrix with other weights
+    is not detected and still matches the oracle."""
+    import torch
+    # kNN Laplacian with vertex 0 cut off (an isolated vertex: an empty CSR row)
+    base = G.knn3d(900, 6, seed=21, shift=0.05).scipy().tocoo()
+    keep = (base.row < base.col) & (base.row != 0) & (base.col != 0)
+    lap = G._from_edges(900, base.row[keep], base.col[keep], 0.05, "knn_cut")
+    assert lap.row_ptr[1] == lap.row_ptr[0]
+    n = lap.n
+    lo, hi = 0.02, 0.9
+    m0, nc = 13, 4
+    q0 = OF.random_start(n, m0, 5)
+    z, w = OQ.nodes(lo, hi, nc, 1.0)
+    p = lib.RAFEAST_FP64 if prec == "fp64" else lib.RAFEAST_MIXED
+    tol, itol = (1e-12, 1e-10) if prec == "fp64" else (1e-5, 2e-4)
+    exp, _ = OF.filter_apply(lap.scipy(), q0, z, w, tol, 4000, "correction")
+    got = {}
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    try:
+        for vf in (0, 1):
+            lib.rafeast_set_option(h, lib.RAFEAST_OPT_VALUES_FREE, vf)
+            Qt = torch.zeros((m0, n), dtype=torch.float64, device="cuda")
+            prm = lib.make_params(lo, hi, m0, nc, 1.0, tol, 1e-10, 1, 4000, p,
+                                  lib.RAFEAST_FORM_CORRECTION)
+            lib.rafeast_filter(h, prm, colmajor_dev(q0), None, Qt)
+            got[vf] = from_colmajor(Qt)
+            assert np.linalg.norm(got[vf] - exp) <= itol * np.linalg.norm(exp), vf
+        assert np.linalg.norm(got[0] - got[1]) <= itol * np.linalg.norm(exp)
+    finally:
+        lib.rafeast_destroy(h)
+    # weights other than -1: no values-free path, same answer as the oracle
+    rng = np.random.default_rng(3)
+    a = lap.scipy().tocsr().copy()
+    off = a.copy()
+    off.setdiag(0)
+    off.eliminate_zeros()
+    off.data[:] = -rng.uniform(0.5, 1.5, off.nnz)
+    off = (off + off.T) * 0.5
+    wl = (sp.diags(-np.asarray(off.sum(axis=1)).ravel()) + off).tocsr()
+    wl.sort_indices()
+    A = wl + lap.shift * sp.identity(n)
+    exp2, _ = OF.filter_apply(A.tocsr(), q0, z, w, tol, 4000, "correction")
+    h = lib.rafeast_create(wl.indptr.astype(np.int32), wl.indices.astype(np.int32),
+                           wl.data.astype(np.float64), lap.shift)
+    try:
+        Qt = torch.zeros((m0, n), dtype=torch.float64, device="cuda")
+        prm = lib.make_params(lo, hi, m0, nc, 1.0, tol, 1e-10, 1, 4000, p,
+                              lib.RAFEAST_FORM_CORRECTION)
+        lib.rafeast_filter(h, prm, colmajor_dev(q0), None, Qt)
+        assert np.linalg.norm(from_colmajor(Qt) - exp2) <= itol * np.linalg.norm(exp2)
+    finally:
+        lib.rafeast_destroy(h)
+
+
 # ---- bulk-copy (TMA) gathers vs register gathers ---------------------------------
 
 def _filter_complex64(A, q0, z, w, steps):
