@@ -13,9 +13,8 @@ Default workload (``knn200k``): kNN graph Laplacian of 200,000 uniform points
 in [0,1]^3 (seed 2), k = 10, union-symmetrised, unit weights, + 1e-3 I; the
 64 smallest eigenvalues; m0 = 80, N_c = 4, p = 20, q = 2, outer tolerance
 1e-11, relaxed inner solves (COCG tolerance 1e-2, at most 100 steps), mixed
-precision (float32 shifted solves, double outer loop). The inputs (COCG state
-4 x n x 640 x 4 B = 2.05 GB) are larger than L2, so no flush is needed
-between steps.
+precision (float32 shifted solves, double outer loop). Every timed step
+starts with a cold L2 (a 512 MB write before it, outside its CUDA events).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -42,6 +41,7 @@ WORKLOADS = {
     "grid3d": dict(key="grid3d", precision="mixed"),
     "knn8k": dict(key="knn8k", precision="fp64"),
     "sbm64": dict(key="sbm64", precision="mixed"),
+    "rgg16k": dict(key="rgg16k", precision="fp64"),
 }
 
 
@@ -247,7 +247,8 @@ def _reference_counts(key):
     # parameters); used only to extrapolate the oracle's bounded sample
     table = {"knn200k": dict(outer=8, cocg_total=800),
              "grid3d": dict(outer=9, cocg_total=900),
-             "knn8k": dict(outer=11, cocg_total=900)}
+             "knn8k": dict(outer=11, cocg_total=900),
+             "rgg16k": dict(outer=4, cocg_total=389)}
     return table[key]
 
 
@@ -259,8 +260,7 @@ def _config(key):
             "count": g["count"], "m0": cfg.m0, "nc": cfg.nc, "p": cfg.p, "q": cfg.q,
             "solve_tol": cfg.solve_tol, "outer_tol": cfg.outer_tol,
             "interval": [g["lmin"], g["lmax"]],
-            "l2": "inputs larger than L2 (no flush): COCG state of 4 arrays n x 2*N_c*m0 "
-                  "float32" if cfg.precision == "mixed" else "L2 flushed between steps"}
+            "l2": "L2 flushed (512 MB write, outside the timed events) before every timed step"}
 
 
 def run_batched(args):
@@ -534,6 +534,63 @@ print(json.dumps(dict(t_ws=t_ws, t_step=t_step, t_rr=t_rr, nnz=a.nnz)))
     return {"est": est, "sample": sample}
 
 
+def _rgg_table(R, h, torch, stream, g, cfg, evals):
+    """Table 1 of the paper on this GPU: standard FEAST (N_c = 8, random start,
+    tight solves, to convergence) and RA-FEAST at N_c = 8, 4, 2 with the
+    iteration limits 2 and 4; time (warm, CUDA events), speedup, maximum
+    absolute eigenvalue error against ARPACK, warmstart (Phase 1) time."""
+    import numpy as np
+    ref = np.array(g["evals"])
+    rows = []
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=evals.device)
+
+    def timed(fn):
+        fn()  # warm
+        flush.fill_(1.0)  # cold L2 for the timed run
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    def solve(nc, max_outer, warm, solve_tol):
+        def fn():
+            t_ws = 0.0
+            if warm:
+                w0 = torch.cuda.Event(enable_timing=True)
+                w1 = torch.cuda.Event(enable_timing=True)
+                w0.record(stream)
+                R.rafeast_warmstart(h, g["lmin"], g["lmax"], cfg.m0, cfg.p, cfg.q, cfg.seed)
+                w1.record(stream)
+                torch.cuda.synchronize()
+                t_ws = w0.elapsed_time(w1)
+            start = R.RAFEAST_START_SUBSPACE if warm else R.RAFEAST_START_RANDOM
+            prm = R.make_params(g["lmin"], g["lmax"], cfg.m0, nc, 1.0, solve_tol, cfg.outer_tol,
+                                max_outer, cfg.max_inner, R.RAFEAST_FP64,
+                                R.RAFEAST_FORM_CORRECTION, start, cfg.seed)
+            st, mf, info = R.rafeast_solve(h, prm, evals, None, None)
+            ev = evals.cpu().numpy()[:mf]
+            err = float(np.max(np.abs(np.sort(ev) - ref))) if mf == len(ref) else None
+            return st, mf, info, err, t_ws
+        return fn
+
+    ms, (st, mf, info, err, _) = timed(solve(8, 40, False, 1e-10))
+    base = ms
+    rows.append({"method": "standard FEAST (N_c=8, random start, COCG to 1e-10)", "ms": ms,
+                 "speedup": 1.0, "max_abs_err": err, "phase1_ms": None,
+                 "outer_iters": info.outer_iters, "status": st})
+    for nc in (8, 4, 2):
+        for mo in (2, 4):
+            ms, (st, mf, info, err, tws) = timed(solve(nc, mo, True, cfg.solve_tol))
+            rows.append({"method": f"RA-FEAST (N_c={nc}, max_iter={mo})", "ms": ms,
+                         "speedup": base / ms, "max_abs_err": err, "phase1_ms": tws,
+                         "outer_iters": info.outer_iters, "status": st})
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,10 +646,14 @@ def main():
 
     infos = []
 
+    # the RGG workloads stop at the paper's iteration limit (status 2 is the
+    # expected outcome there); the others must converge
+    ok_status = (R.RAFEAST_OK, R.RAFEAST_NO_CONVERGENCE) if key.startswith("rgg") else (R.RAFEAST_OK,)
+
     def step(p=prec):
         R.rafeast_warmstart(h, lmin, lmax, m0, cfg.p, cfg.q, cfg.seed)
         st, mf, info = R.rafeast_solve(h, params(p), evals, evecs, resid)
-        if st != R.RAFEAST_OK:
+        if st not in ok_status:
             raise RuntimeError(f"solve status {st}: {info.as_dict()}")
         infos.append((mf, info))
         return mf, info
@@ -608,17 +669,23 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    # every timed step starts with a cold L2: a 512 MB write (more than the
+    # 126 MB L2) before it, outside its CUDA-event pair
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
+    ms = 0.0
     for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
     if dist:
         dist.barrier()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    del flush
     prof = R.rafeast_profile(h, reset=True)
     R.rafeast_set_option(h, R.RAFEAST_OPT_PROFILE, 0)
     ms = max_over_ranks(ms, dist, dev)
@@ -669,6 +736,19 @@ def main():
             "outer_iters": info.outer_iters, "cocg_iters_total": info.cocg_iters_total,
             "phases_ms": phases, "roofline": roofline, "gpu_launches": int(launches),
             "clocks": ck}
+
+    # COCG working set: seed r, p, w, s and the shifted directions (complex)
+    # plus the quadrature sum
+    sv = 4 if prec == R.RAFEAST_MIXED else 8
+    pairs = (m0 + 1) // 2
+    ws_bytes = n * 2 * pairs * 2 * sv * (4 + (cfg.nc - 1)) + n * 2 * pairs * sv
+    if ws_bytes < 126e6:
+        line["roofline"]["note"] = (f"COCG working set {ws_bytes / 1e6:.0f} MB fits the 126 MB L2 "
+                                    "after the first step: the HBM roofline does not bind")
+    if key.startswith("rgg"):
+        line["parity"]["max_abs_err_vs_arpack"] = (float(np.max(np.abs(np.sort(ev) - ref)))
+                                                   if mf == len(ref) else None)
+        line["table"] = _rgg_table(R, h, torch, stream, g, cfg, evals)
 
     # FP64 comparison (same workload, same stream; one untimed-warm step)
     if not args.no_fp64 and prec == R.RAFEAST_MIXED:

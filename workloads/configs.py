@@ -19,6 +19,11 @@ too, so every consumer reads the same numbers.
 * ``grid3d``  RA-FEAST, mixed: 3-D 7-point grid 100^3 (n=1e6, nnz=6.94e6)
   + 1e-2 I, 63 eigenvalues in [0.005, 0.0272568], m0=96, N_c=4, p=20, q=2,
   inner solves as ``knn200k``, outer tolerance 1e-10.
+* ``rgg2k``, ``rgg8k``, ``rgg16k``: the paper's own workload (Section 5.1),
+  random geometric graphs in the unit square with r = 1.5 sqrt(log n / n),
+  L = D - A, the eigenvalues in [0.001, 5.0] (12, 29, 46 of them), subspace
+  1.5 x count, RA-FEAST FP64 at N_c = 2, p=10, q=2, COCG tolerance 1e-4,
+  max_iter = 4.
 * ``sbm64``   batched RA-FEAST, mixed: 64 stochastic-block-model Laplacians
   + 1e-3 I, n log-uniform in [2000, 300000] (seed 4), 4..16 blocks,
   p_in = 20/n_block, p_out = 1/n, k = blocks + 8, m0 = ceil(1.5 k), N_c=2;
@@ -82,6 +87,21 @@ def _cfgs():
         "grid3d": Config("grid3d", lambda: graphs.grid3d(100, 100, 100, 1e-2), 63, 96, 4,
                          "mixed", 1e-2, 1e-10, "correction", True, p=20, q=2, seed=3,
                          max_inner=100, description="RA-FEAST mixed, 3-D grid 100^3"),
+        # the paper's experiment (Section 5.1): random geometric graph in the
+        # unit square, r = 1.5 sqrt(log n / n), L = D - A (no shift), the
+        # eigenvalues in [0.001, 5.0]; subspace 1.5 x their count (46 at
+        # n = 16,000); RA-FEAST FP64 with relaxed solves and the paper's
+        # iteration limit max_iter = 4 (bench.py adds the other N_c / max_iter
+        # rows of Table 1 and standard FEAST)
+        "rgg16k": Config("rgg16k", lambda: graphs.rgg2d(16000, seed=0), 46, 69, 2, "fp64",
+                         1e-4, 1e-10, "correction", True, p=10, q=2, seed=1, max_outer=4,
+                         max_inner=2000, description="RA-FEAST FP64, RGG n=16000 (Section 5.1)"),
+        "rgg2k": Config("rgg2k", lambda: graphs.rgg2d(2000, seed=0), 12, 18, 2, "fp64",
+                        1e-4, 1e-10, "correction", True, p=10, q=2, seed=1, max_outer=4,
+                        max_inner=2000, description="RA-FEAST FP64, RGG n=2000 (Section 5.1)"),
+        "rgg8k": Config("rgg8k", lambda: graphs.rgg2d(8000, seed=0), 29, 44, 2, "fp64",
+                        1e-4, 1e-10, "correction", True, p=10, q=2, seed=1, max_outer=4,
+                        max_inner=2000, description="RA-FEAST FP64, RGG n=8000 (Section 5.1)"),
     }
 
 
