@@ -146,7 +146,11 @@ typedef struct rafeast_info {
   int32_t kernel_launches;   /* kernels launched by this call                 */
   int32_t spmm_launches;     /* of which sparse-matrix products               */
   double max_resid;          /* max in-interval relative residual             */
-  double t_warmstart_ms;     /* device time per phase (CUDA events)           */
+  double t_warmstart_ms;     /* device time per phase (CUDA events). This one */
+                             /* is the start phase of the solve call: random  */
+                             /* start (Omega, orthonormalise, A Q) or the     */
+                             /* check of the handle's subspace; the time of   */
+                             /* a rafeast_warmstart call is not in it         */
   double t_filter_ms;
   double t_orth_ms;
   double t_rr_ms;

@@ -285,23 +285,29 @@ void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
 // ---------------------------------------------------------------------------
 // tall GEMM: Y[r][b] = sum_a X[r][a] M[a][b]   (M row-major m x mo)
 // ---------------------------------------------------------------------------
-constexpr int GEMM_ROWS = 8;
+// A row of Y is computed by L = ceil(mo / V) threads, V columns each
+// (b = lane + L v), so that few lanes idle when mo is not a multiple of 32
+// (mo = 80: 27 lanes, 81 slots); a CTA of 256 threads takes 256 / L rows
+// (at most GEMM_MAX_ROWS) per tile. Rows of a tile may straddle warps.
+constexpr int GEMM_MAX_ROWS = 32;
 
-// UPPER: M is upper triangular (M[a][b] = 0 for a > b): column block v of
-// 32 columns needs rows a < 32 v + 32 only (a warp-uniform bound)
+// UPPER: M is upper triangular (M[a][b] = 0 for a > b): column block v
+// (b < L v + L) needs rows a < L v + L only, a bound shared by the row's lanes
 template <int V, bool UPPER>
 __global__ void __launch_bounds__(256) k_tall_gemm(const double* __restrict__ X, int64_t n, int m,
                                                    int ldx, const double* __restrict__ M, int mo,
                                                    double* __restrict__ Y, int ldy) {
   extern __shared__ double tsm[];
+  const int L = (mo + V - 1) / V;
+  const int rpt = min(GEMM_MAX_ROWS, (int)blockDim.x / L);  // rows per tile
   double* Ms = tsm;              // m * mo
-  double* Xs = tsm + m * mo;     // GEMM_ROWS * m
+  double* Xs = tsm + m * mo;     // rpt * m
   for (int t = threadIdx.x; t < m * mo; t += blockDim.x) Ms[t] = M[t];
-  const int tr = threadIdx.x >> 5, tc = threadIdx.x & 31;
-  for (int64_t rb = blockIdx.x * (int64_t)GEMM_ROWS; rb < n; rb += (int64_t)gridDim.x * GEMM_ROWS) {
+  const int tr = threadIdx.x / L, tc = threadIdx.x - (threadIdx.x / L) * L;
+  for (int64_t rb = blockIdx.x * (int64_t)rpt; rb < n; rb += (int64_t)gridDim.x * rpt) {
     __syncthreads();
-    const int rows = (int)min((int64_t)GEMM_ROWS, n - rb);
-    for (int t = threadIdx.x; t < GEMM_ROWS * m; t += blockDim.x) {
+    const int rows = (int)min((int64_t)rpt, n - rb);
+    for (int t = threadIdx.x; t < rpt * m; t += blockDim.x) {
       const int rr = t / m;
       Xs[t] = rr < rows ? X[(rb + rr) * ldx + (t - rr * m)] : 0.0;
     }
@@ -314,14 +320,14 @@ __global__ void __launch_bounds__(256) k_tall_gemm(const double* __restrict__ X,
         const double x = Xs[tr * m + a];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          const int b = tc + 32 * v;
-          if (UPPER && a >= 32 * v + 32) continue;
+          const int b = tc + L * v;
+          if (UPPER && a >= L * v + L) continue;
           if (b < mo) acc[v] = fma(x, Ms[a * mo + b], acc[v]);
         }
       }
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        const int b = tc + 32 * v;
+        const int b = tc + L * v;
         if (b < mo) Y[(rb + tr) * ldy + b] = acc[v];
       }
     }
@@ -331,11 +337,13 @@ __global__ void __launch_bounds__(256) k_tall_gemm(const double* __restrict__ X,
 void tall_gemm(const double* X, int64_t n, int m, int ldx, const double* M, int mo, double* Y,
                int ldy, cudaStream_t s, bool upper) {
   const int V = (mo + 31) / 32;
-  const size_t smem = ((size_t)m * mo + (size_t)GEMM_ROWS * m) * sizeof(double);
+  const int L = (mo + V - 1) / V;
+  const int rpt = std::min(GEMM_MAX_ROWS, 256 / L);
+  const size_t smem = ((size_t)m * mo + (size_t)rpt * m) * sizeof(double);
   int dev = 0, sms = 0;
   RF_CUDA(cudaGetDevice(&dev));
   RF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t tiles = (n + GEMM_ROWS - 1) / GEMM_ROWS;
+  const int64_t tiles = (n + rpt - 1) / rpt;
   int blocks = (int)std::min<int64_t>(tiles, (int64_t)sms * 2);
   if (blocks < 1) blocks = 1;
   switch (V) {
@@ -536,9 +544,12 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
       // the pairs of a round are disjoint, so every 2 x 2 block (rows of
       // pair j, columns of pair k) is updated on its own from its old
       // values: B <- L_j B R_k with L = [[c, -s], [s, c]], R = L^T; the
-      // rotated diagonal blocks lose their off-diagonal entry
+      // rotated diagonal blocks lose their off-diagonal entry. A stays
+      // symmetric, so block (k, j) is written as the transpose of block
+      // (j, k) and only the blocks j <= k are computed.
       for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
         const int j = t / np, k = t % np;
+        if (j > k) continue;
         const T cj = cs[2 * j], sj = cs[2 * j + 1];
         const T ck = cs[2 * k], sk = cs[2 * k + 1];
         if (sj == (T)0 && sk == (T)0) continue;
@@ -550,10 +561,21 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
         const T b11 = cj * a11 - sj * a21, b12 = cj * a12 - sj * a22;
         const T b21 = sj * a11 + cj * a21, b22 = sj * a12 + cj * a22;
         // columns: (L_j B) R_k
-        A[pj * me + pk] = ck * b11 - sk * b12;
-        A[pj * me + qk] = j == k ? (T)0 : sk * b11 + ck * b12;
-        A[qj * me + pk] = j == k ? (T)0 : ck * b21 - sk * b22;
-        A[qj * me + qk] = sk * b21 + ck * b22;
+        const T n11 = ck * b11 - sk * b12, n22 = sk * b21 + ck * b22;
+        A[pj * me + pk] = n11;
+        A[qj * me + qk] = n22;
+        if (j == k) {
+          A[pj * me + qk] = (T)0;
+          A[qj * me + pk] = (T)0;
+        } else {
+          const T n12 = sk * b11 + ck * b12, n21 = ck * b21 - sk * b22;
+          A[pj * me + qk] = n12;
+          A[qj * me + pk] = n21;
+          A[pk * me + pj] = n11;
+          A[qk * me + pj] = n12;
+          A[pk * me + qj] = n21;
+          A[qk * me + qj] = n22;
+        }
       }
       // V R_k
       for (int t = threadIdx.x; t < np * me; t += blockDim.x) {

@@ -184,6 +184,52 @@ def test_rayleigh_ritz(lib, m):
 
 # ---- a1 + a4..a7: the quadrature filter (batched COCG) ---------------------------
 
+# ---- a2/a3: warmstart (powers of B, orthonormalisation, Ritz selection) -----------
+
+# (name, matrix, interval, m0, p, q, map option: 0 auto, 1 literal, 2 low-end)
+_WS_CASES = [
+    ("grid40x50", lambda: G.grid2d(40, 50, 0.0), (0.0019733, 0.0792439), 24, 10, 2, 0),
+    ("knn2000", lambda: G.knn3d(2000, 10, 5, 1e-3), (5e-4, 0.3), 24, 10, 2, 0),
+    ("knn2000_odd", lambda: G.knn3d(2000, 10, 5, 1e-3), (5e-4, 0.3), 23, 8, 2, 2),
+    ("knn2000_p0q0", lambda: G.knn3d(2000, 10, 5, 1e-3), (5e-4, 0.3), 24, 0, 0, 0),
+    ("knn2000_literal", lambda: G.knn3d(2000, 10, 5, 1e-3), (5e-4, 0.3), 24, 10, 1, 1),
+    ("rgg2000", lambda: G.rgg2d(2000, seed=3), (0.001, 5.0), 18, 10, 2, 0),
+]
+
+
+@pytest.mark.parametrize("case", _WS_CASES, ids=[c[0] for c in _WS_CASES])
+def test_warmstart_matches_oracle(lib, case):
+    """rafeast_warmstart against the oracle's Phase 1 on the same Philox Omega:
+    the kept Ritz values and the span of the kept Ritz vectors. The oracle
+    orthonormalises by Householder QR, the library by Cholesky-QR; both give
+    the same spans, and on these cases a Cholesky-QR variant of the oracle
+    differs from it by at most 6e-14 in sin-theta, so the bounds leave three
+    to four orders of margin for the other rounding differences (SpMM order,
+    Omega within 1e-13, the Jacobi eigensolver)."""
+    name, make, (lmin, lmax), m0, p, q, which = case
+    lap = make()
+    a = lap.scipy()
+    seed = 11
+    om = OP.gaussian_matrix(lap.n, m0 + p, seed)
+    wmap = {0: "auto", 1: "literal", 2: "low"}[which]
+    q0, th0, info = OF.warmstart(a, lmin, lmax, m0, p, q, om, wmap)
+    # the selection of m0 of the m0+p Ritz values must be well defined
+    d = np.sort(np.abs(info["ritz_all"] - 0.5 * (lmin + lmax)))
+    assert p == 0 or d[m0] - d[m0 - 1] > 1e-6
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    try:
+        lib.rafeast_set_option(h, lib.RAFEAST_OPT_WARMSTART_MAP, which)
+        lib.rafeast_warmstart(h, lmin, lmax, m0, p, q, seed)
+        Q = np.zeros((m0, lap.n))
+        th = lib.rafeast_get_subspace(h, Q, m0)
+        qg = Q.T.copy()
+        assert np.max(np.abs(th - th0)) <= 1e-11 * np.max(np.abs(th0))
+        assert M.orth_err(qg) < 1e-12
+        assert M.sin_theta(qg, q0) <= 1e-9
+    finally:
+        lib.rafeast_destroy(h)
+
+
 def _filter_case():
     dims = (14, 17)
     lap = G.grid2d(*dims, shift=0.0)
