@@ -35,6 +35,10 @@ sys.path.insert(0, ROOT)
 METRIC = ("RA-FEAST time-to-solution & SpMM HBM GB/s, FP32-mixed vs FP64, "
           "eig relerr≤1e-8")
 FALLBACK_HBM_GBS = 6800.0
+# FP64 issue rate of the part: the nominal 1.25 TFLOP/s FP64 (an FMA counted
+# as 2 flops) over 152 SMs at 2070 MHz is 2 FP64 lane operations (an add or an
+# FMA each) per SM per clock
+FP64_OPS_PER_SM_CLK = 2.0
 
 WORKLOADS = {
     "knn200k": dict(key="knn200k", precision="mixed"),
@@ -534,11 +538,60 @@ print(json.dumps(dict(t_ws=t_ws, t_step=t_step, t_rr=t_rr, nnz=a.nnz)))
     return {"est": est, "sample": sample}
 
 
+def _fp64_dots_roofline(hbm, prof, lap, dev):
+    """The FP64 seed dot kernel is bound by the FP64 pipe, not by HBM: every
+    gathered real entry costs one FP64 add (values-free) or FMA, 1.25 TFLOP/s
+    nominal on this part against 64x that for FP32. Its FP64 lane operations
+    per launch: per active column pair, 4 per gathered entry (two complex
+    columns, real and imaginary parts) and 32 per row (L r from the sum,
+    w = z r - L r, the five dot products). The active pairs come from the
+    library's byte count of the same launches (A once plus, per pair, r read
+    and w written)."""
+    import numpy as np
+    import torch
+    n = lap.n
+    rp = lap.row_ptr.astype(np.int64)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    diag = rows == lap.col_idx
+    off = ~diag
+    deg = np.diff(rp) - np.bincount(rows[diag], minlength=n)
+    vf = bool(np.all(lap.values[off] == -1.0)
+              and np.all(lap.values[diag] == deg[rows[diag]]))
+    nnz_off = int(off.sum())
+    abytes = (nnz_off * 4.0 if vf else lap.nnz * 12.0) + 4.0 * (n + 1)
+    pairb = n * 2 * 2.0 * 8.0
+    launches = max(prof["dots_launches"], 1.0)
+    act_pairs = (prof["dots_bytes"] - launches * abytes) / (2.0 * pairb)
+    gathered = nnz_off if vf else lap.nnz
+    ops = act_pairs * (4.0 * gathered + 32.0 * n)
+    ms = prof["dots_ms"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = 2070.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    peak = sms * FP64_OPS_PER_SM_CLK * mhz * 1e6 / 1e9
+    achieved = ops / (ms * 1e-3) / 1e9
+    out = {"bound": "alu", "kernel": hbm["kernel"], "achieved": achieved, "peak": peak,
+           "peak_kind": (f"derived: {sms} SMs x {FP64_OPS_PER_SM_CLK:g} FP64 ops/clk x "
+                         f"{mhz:g} MHz (nominal 1.25 TFLOP/s FP64)"),
+           "unit": "G FP64 ops/s (an add or an FMA = 1)", "frac": achieved / peak,
+           "traffic": None, "fp64_ops_per_launch": ops / launches,
+           "ms_per_launch": hbm["ms_per_launch"], "launches": hbm["launches"],
+           "shapes": hbm["shapes"], "other_kernel": hbm["other_kernel"],
+           "share_of_step": hbm["share_of_step"],
+           "hbm_view": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac",
+                                            "algorithmic_bytes_per_launch")}}
+    return out
+
+
 def _rgg_table(R, h, torch, stream, g, cfg, evals):
     """Table 1 of the paper on this GPU: standard FEAST (N_c = 8, random start,
     tight solves, to convergence) and RA-FEAST at N_c = 8, 4, 2 with the
-    iteration limits 2 and 4; time (warm, CUDA events), speedup, maximum
-    absolute eigenvalue error against ARPACK, warmstart (Phase 1) time."""
+    iteration limits 2 and 4, in FP64 and with float32 shifted solves; time
+    (warm, CUDA events), speedup, maximum absolute eigenvalue error against
+    ARPACK, warmstart (Phase 1) time."""
     import numpy as np
     ref = np.array(g["evals"])
     rows = []
@@ -556,7 +609,7 @@ def _rgg_table(R, h, torch, stream, g, cfg, evals):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), out
 
-    def solve(nc, max_outer, warm, solve_tol):
+    def solve(nc, max_outer, warm, solve_tol, prec=R.RAFEAST_FP64, max_inner=cfg.max_inner):
         def fn():
             t_ws = 0.0
             if warm:
@@ -569,9 +622,12 @@ def _rgg_table(R, h, torch, stream, g, cfg, evals):
                 t_ws = w0.elapsed_time(w1)
             start = R.RAFEAST_START_SUBSPACE if warm else R.RAFEAST_START_RANDOM
             prm = R.make_params(g["lmin"], g["lmax"], cfg.m0, nc, 1.0, solve_tol, cfg.outer_tol,
-                                max_outer, cfg.max_inner, R.RAFEAST_FP64,
+                                max_outer, max_inner, prec,
                                 R.RAFEAST_FORM_CORRECTION, start, cfg.seed)
-            st, mf, info = R.rafeast_solve(h, prm, evals, None, None)
+            try:
+                st, mf, info = R.rafeast_solve(h, prm, evals, None, None)
+            except R.RafeastError as exc:
+                return exc.code, 0, None, None, t_ws
             ev = evals.cpu().numpy()[:mf]
             err = float(np.max(np.abs(np.sort(ev) - ref))) if mf == len(ref) else None
             return st, mf, info, err, t_ws
@@ -581,13 +637,25 @@ def _rgg_table(R, h, torch, stream, g, cfg, evals):
     base = ms
     rows.append({"method": "standard FEAST (N_c=8, random start, COCG to 1e-10)", "ms": ms,
                  "speedup": 1.0, "max_abs_err": err, "phase1_ms": None,
-                 "outer_iters": info.outer_iters, "status": st})
+                 "outer_iters": info.outer_iters if info else None, "status": st})
     for nc in (8, 4, 2):
         for mo in (2, 4):
             ms, (st, mf, info, err, tws) = timed(solve(nc, mo, True, cfg.solve_tol))
             rows.append({"method": f"RA-FEAST (N_c={nc}, max_iter={mo})", "ms": ms,
                          "speedup": base / ms, "max_abs_err": err, "phase1_ms": tws,
-                         "outer_iters": info.outer_iters, "status": st})
+                         "outer_iters": info.outer_iters if info else None, "status": st})
+    # the same with float32 shifted solves (the outer loop stays FP64): FP64
+    # runs at 1/64 of the FP32 rate on this part, and the gathers of a dense
+    # RGG row are FP64-issue bound. Float32 COCG keeps the 100-step cap of the
+    # other mixed workloads (past it the float recurrences lose their
+    # bi-orthogonality and may break down).
+    for nc in (8, 4, 2):
+        for mo in (2, 4):
+            ms, (st, mf, info, err, tws) = timed(solve(nc, mo, True, cfg.solve_tol,
+                                                       R.RAFEAST_MIXED, 100))
+            rows.append({"method": f"RA-FEAST mixed (N_c={nc}, max_iter={mo}, COCG <= 100 steps)",
+                         "ms": ms, "speedup": base / ms, "max_abs_err": err, "phase1_ms": tws,
+                         "outer_iters": info.outer_iters if info else None, "status": st})
     return rows
 
 
@@ -736,6 +804,9 @@ def main():
                                  / 1e6,
                                  "ms_per_launch": prof[f"{other}_ms"] / max(prof[f"{other}_launches"], 1)},
                 "share_of_step": (prof["update_ms"] + prof["dots_ms"]) / ms}
+
+    if prec == R.RAFEAST_FP64 and pre == "dots":
+        roofline = _fp64_dots_roofline(roofline, prof, lap, dev)
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,

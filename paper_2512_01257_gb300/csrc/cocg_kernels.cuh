@@ -22,7 +22,11 @@ template <> constexpr int maxcpl_of<double>(int NC) { return NC >= 8 ? 1 : 8 / N
 // resident warps) used when the chosen shape needs no more chunks than it has
 template <typename T> constexpr int small_cpl_of(int NC);
 template <> constexpr int small_cpl_of<float>(int NC) { return NC >= 4 ? 1 : 4 / NC; }
-template <> constexpr int small_cpl_of<double>(int NC) { return NC >= 8 ? 1 : 8 / NC; }
+// (double column pairs of the multi-shift seed: 2 chunks, which is all the
+// FP64 shapes use, at 2 CTAs per SM instead of 4 chunks at 1)
+template <> constexpr int small_cpl_of<double>(int NC) {
+  return NC == 2 ? 2 : (NC >= 8 ? 1 : 8 / NC);
+}
 
 
 template <typename K>

@@ -544,12 +544,9 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
       // the pairs of a round are disjoint, so every 2 x 2 block (rows of
       // pair j, columns of pair k) is updated on its own from its old
       // values: B <- L_j B R_k with L = [[c, -s], [s, c]], R = L^T; the
-      // rotated diagonal blocks lose their off-diagonal entry. A stays
-      // symmetric, so block (k, j) is written as the transpose of block
-      // (j, k) and only the blocks j <= k are computed.
+      // rotated diagonal blocks lose their off-diagonal entry
       for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
         const int j = t / np, k = t % np;
-        if (j > k) continue;
         const T cj = cs[2 * j], sj = cs[2 * j + 1];
         const T ck = cs[2 * k], sk = cs[2 * k + 1];
         if (sj == (T)0 && sk == (T)0) continue;
@@ -561,21 +558,10 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
         const T b11 = cj * a11 - sj * a21, b12 = cj * a12 - sj * a22;
         const T b21 = sj * a11 + cj * a21, b22 = sj * a12 + cj * a22;
         // columns: (L_j B) R_k
-        const T n11 = ck * b11 - sk * b12, n22 = sk * b21 + ck * b22;
-        A[pj * me + pk] = n11;
-        A[qj * me + qk] = n22;
-        if (j == k) {
-          A[pj * me + qk] = (T)0;
-          A[qj * me + pk] = (T)0;
-        } else {
-          const T n12 = sk * b11 + ck * b12, n21 = ck * b21 - sk * b22;
-          A[pj * me + qk] = n12;
-          A[qj * me + pk] = n21;
-          A[pk * me + pj] = n11;
-          A[qk * me + pj] = n12;
-          A[pk * me + qj] = n21;
-          A[qk * me + qj] = n22;
-        }
+        A[pj * me + pk] = ck * b11 - sk * b12;
+        A[pj * me + qk] = j == k ? (T)0 : sk * b11 + ck * b12;
+        A[qj * me + pk] = j == k ? (T)0 : ck * b21 - sk * b22;
+        A[qj * me + qk] = sk * b21 + ck * b22;
       }
       // V R_k
       for (int t = threadIdx.x; t < np * me; t += blockDim.x) {

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(THREADS) k_cocg_init(CocgArgs<T> a) {
 // COCG dots kernel
 // ---------------------------------------------------------------------------
 template <typename T, int NC, int MAXCPL, bool VF = false>
-__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && MAXCPL * NC <= 4) ? 2 : 1)
+__global__ void __launch_bounds__(THREADS, (MAXCPL * NC <= 4) ? 2 : 1)
     k_cocg_dots(CocgArgs<T> a, int buf) {
   cocg_dots_body<T, NC, MAXCPL, VF>(a, &a, buf, grid_blk());
 }
