@@ -772,13 +772,18 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
     }
   if (!have && h->opt_autotune && !h->opt_lanes && !h->opt_cpl) {
     // (lanes, chunks, CTAs per SM; 0 = the default instance)
+    // (the last three only for FP64, whose one-chunk dot instance runs at
+    // 3 CTAs per SM)
     const int cand[][3] = {{32, 2, 0}, {16, 2, 0}, {16, 3, 0}, {16, 4, 0}, {8, 1, 0},
                            {8, 2, 0},  {8, 4, 0},  {4, 2, 0},  {32, 2, 3}, {16, 2, 3},
                            {8, 2, 3},  {16, 2, 4}, {16, 3, 2}, {16, 4, 2}, {8, 3, 2},
-                           {8, 4, 2},  {16, 3, 3}};
+                           {8, 4, 2},  {16, 3, 3}, {4, 1, 0},  {16, 1, 0}, {32, 1, 0}};
+    const int n_all = (int)(sizeof(cand) / sizeof(cand[0])), n_fp64_only = 3;
     float best_d = 1e30f, best_u = 1e30f;
-    for (auto& c : cand) {
+    for (int ci = 0; ci < n_all; ++ci) {
+      const int* c = cand[ci];
       if (ctl.done) break;
+      if (!fp64 && ci >= n_all - n_fp64_only) continue;
       const int G = c[0], cpl = c[1];
       if (cpl > cap) continue;
       if (c[2] && fp64) continue;

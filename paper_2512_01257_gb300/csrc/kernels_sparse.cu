@@ -503,6 +503,9 @@ static void dispatch_dots_mc(const CocgArgs<T>& a, int buf, int num_sms, cudaStr
         kern = a.occ >= 4 ? (vf ? k_cocg_dots_occ<T, MC, 4, true> : k_cocg_dots_occ<T, MC, 4>)
                           : (vf ? k_cocg_dots_occ<T, MC, 3, true> : k_cocg_dots_occ<T, MC, 3>);
     }
+    // double, one chunk per lane: compiled for 3 CTAs per SM
+    if constexpr (MC == 1 && sizeof(T) == 8)
+      kern = vf ? k_cocg_dots_occ<T, 1, 3, true> : k_cocg_dots_occ<T, 1, 3>;
     if constexpr ((MC == 3 || MC == 4) && sizeof(T) == 4) {
       if (a.occ >= 2)
         kern = a.occ >= 3 ? (vf ? k_cocg_dots_occ<T, MC, 3, true> : k_cocg_dots_occ<T, MC, 3>)
@@ -543,6 +546,13 @@ static void dispatch_dots(const CocgArgs<T>& a, int buf, int num_sms, cudaStream
     if (a.occ >= 2 && a.cpl > SC && a.cpl <= 4) {
       if (a.cpl == 3) dispatch_dots_mc<T, NC, 3>(a, buf, num_sms, s);
       else dispatch_dots_mc<T, NC, 4>(a, buf, num_sms, s);
+      return;
+    }
+  }
+  // double column pairs, one chunk per lane: fewest registers, most warps
+  if constexpr (NC == 2 && sizeof(T) == 8) {
+    if (a.cpl == 1) {
+      dispatch_dots_mc<T, NC, 1>(a, buf, num_sms, s);
       return;
     }
   }
