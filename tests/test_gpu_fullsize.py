@@ -1,0 +1,108 @@
+"""Parity at the full benchmark sizes, in the configuration bench.py times
+(the same workloads, parameters, warmstart seeds and autotuned shapes).
+
+The oracle cannot run these solves in a test's time, so the checks are the
+properties that hold at any size, computed on the host in FP64 from the
+eigenpairs the library returns:
+* every eigenvalue of the interval found, each against the stored ARPACK or
+  closed-form spectrum;
+* the residual ||A v - lambda v||_2 / ||A||_1 of every returned pair,
+  recomputed with scipy;
+* orthonormality of the returned vectors;
+* the eigenspace: sin-theta against the closed-form eigenvectors of the 3-D
+  grid; for the kNN graph, which has no reference vectors, the Davis-Kahan
+  bound sin-theta <= ||R||_F / delta (delta: distance of the returned values
+  to the nearest eigenvalue outside the interval, from the stored spectrum)."""
+import numpy as np
+import pytest
+
+from oracle import exact as E
+from oracle import metrics as M
+from workloads import configs as CF
+
+pytestmark = pytest.mark.gpu
+
+
+def _checks(a, lam, vec, ref, outside, outer_tol, vec_ref=None):
+    """Host FP64 checks of one problem's returned pairs (lam ascending,
+    vec n x m); returns the eigenspace error measure."""
+    norm1 = abs(a).sum(axis=0).max()
+    assert M.eig_relerr(lam, ref) <= 1e-8
+    r = a @ vec - vec * lam
+    res = np.linalg.norm(r, axis=0) / norm1
+    # the library stops at outer_tol on its own FP64 residuals; recomputed
+    # here in another summation order they agree to rounding
+    assert np.all(res <= 2.0 * outer_tol), res.max()
+    assert M.orth_err(vec) <= 1e-10
+    if vec_ref is not None:
+        return M.sin_theta(vec, vec_ref)
+    delta = min(abs(o - lam).min() for o in outside)
+    return float(np.linalg.norm(r) / delta)
+
+
+@pytest.mark.parametrize("key", ["knn200k", "grid3d"])
+def test_single_problem_full_size(lib, key):
+    cfg = CF.CONFIGS[key]
+    g = CF.load_golden()[key]
+    lap = cfg.make()
+    assert lap.checksum() == g["checksum"]
+    h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+    try:
+        lib.rafeast_warmstart(h, g["lmin"], g["lmax"], cfg.m0, cfg.p, cfg.q, cfg.seed)
+        prm = lib.make_params(g["lmin"], g["lmax"], cfg.m0, cfg.nc, cfg.e, cfg.solve_tol,
+                              cfg.outer_tol, cfg.max_outer, cfg.max_inner, lib.RAFEAST_MIXED,
+                              lib.RAFEAST_FORM_CORRECTION, lib.RAFEAST_START_SUBSPACE)
+        evals = np.zeros(cfg.m0)
+        evecs = np.zeros((cfg.m0, lap.n))
+        resid = np.zeros(cfg.m0)
+        st, mf, info = lib.rafeast_solve(h, prm, evals, evecs, resid)
+    finally:
+        lib.rafeast_destroy(h)
+    assert st == lib.RAFEAST_OK, info.as_dict()
+    assert mf == g["count"]
+    lam, vec = evals[:mf], evecs[:mf].T
+    vec_ref = None
+    if key == "grid3d":
+        ref_vals, vec_ref = E.grid_eigvecs_in((100, 100, 100), 1e-2, g["lmin"], g["lmax"])
+        assert len(ref_vals) == g["count"]
+    err = _checks(lap.scipy(), lam, vec, g["evals"], g["neighbours"][:1], cfg.outer_tol, vec_ref)
+    # mixed-path gate on the eigenspace (sin-theta <= 1e-6) where reference
+    # vectors exist; the Davis-Kahan bound is a guaranteed upper bound, which
+    # the stopping tolerance alone keeps below 1e-5 on the kNN graph
+    assert err <= (1e-6 if vec_ref is not None else 1e-5), err
+
+
+def test_batched_sbm_full_size(lib):
+    """All 64 problems of the batched sweep in one rafeast_solve_batched call,
+    each checked against its stored Lanczos spectrum."""
+    S = CF.SBM_SOLVE
+    gold = CF.load_golden()["sbm64"]["instances"]
+    insts = CF.sbm_instances()
+    laps = [CF.make_sbm(i) for i in insts]
+    hs, prms = [], []
+    try:
+        for lap, i, g in zip(laps, insts, gold):
+            assert lap.checksum() == g["checksum"]
+            h = lib.rafeast_create(lap.row_ptr, lap.col_idx, lap.values, lap.shift)
+            hs.append(h)
+            lib.rafeast_warmstart(h, g["lmin"], g["lmax"], i["m0"], S["p"], S["q"], i["seed"])
+            prms.append(lib.make_params(g["lmin"], g["lmax"], i["m0"], S["nc"], S["e"],
+                                        S["solve_tol"], S["outer_tol"], S["max_outer"],
+                                        S["max_inner"], lib.RAFEAST_MIXED,
+                                        lib.RAFEAST_FORM_CORRECTION, lib.RAFEAST_START_SUBSPACE))
+        ev = [np.zeros(i["m0"]) for i in insts]
+        vec = [np.zeros((i["m0"], lap.n)) for i, lap in zip(insts, laps)]
+        res = [np.zeros(i["m0"]) for i in insts]
+        st, mf, info = lib.rafeast_solve_batched(hs, prms, ev, vec, res)
+    finally:
+        for h in hs:
+            lib.rafeast_destroy(h)
+    for t, (lap, g) in enumerate(zip(laps, gold)):
+        assert st[t] == lib.RAFEAST_OK, (t, st[t])
+        assert mf[t] == g["count"], (t, mf[t])
+        m = mf[t]
+        # (no eigenspace bound here: with gaps down to 3.7e-4 after the
+        # interval, outer tolerance 1e-10 guarantees only ~1e-4 by
+        # Davis-Kahan; eigenvalues, residuals and orthonormality are checked)
+        _checks(lap.scipy(), ev[t][:m], vec[t][:m].T, g["evals"], g["neighbours"][:1],
+                S["outer_tol"])
