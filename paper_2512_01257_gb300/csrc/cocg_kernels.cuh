@@ -45,7 +45,8 @@ static inline int grid_x(K kernel, size_t smem, int num_sms, int64_t rows_needed
 // gather core. The G lanes of a group own one row: they load up to G CSR
 // entries of the row at once (coalesced) and broadcast them with width-G
 // shuffles, so the gathered loads of consecutive entries do not wait on each
-// other's index loads; two entries are in flight per step.
+// other's index loads; NB entries (2, or 4 in the narrow float dot kernels)
+// are in flight per step.
 // acc[c][j] += sum_k val_k * X[col_k][chunk c] for the lane's active chunks.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned group_mask(int G) {
@@ -54,7 +55,11 @@ __device__ __forceinline__ unsigned group_mask(int G) {
   return ((1u << G) - 1u) << (grp * G);
 }
 
-template <typename T, int NC, int MAXCPL>
+// NB entries of the row are gathered per step (their loads in flight
+// together); the sums are accumulated entry by entry in CSR order for any NB,
+// so NB changes the latency hiding, not the result. A missing entry at the end
+// re-reads the first entry's row with weight zero.
+template <typename T, int NC, int MAXCPL, int NB = 2>
 __device__ __forceinline__ void gather_row(const int32_t* __restrict__ colidx,
                                            const T* __restrict__ val, int k0, int k1, int row,
                                            int lg, int G, unsigned gmask,
@@ -67,26 +72,31 @@ __device__ __forceinline__ void gather_row(const int32_t* __restrict__ colidx,
     const int my_c = kk < k1 ? __ldg(colidx + kk) : row;
     const T my_v = kk < k1 ? __ldg(val + kk) : (T)0;
     const int cnt = min(G, k1 - kb);
-    for (int e = 0; e < cnt; e += 2) {
-      const int ca = __shfl_sync(gmask, my_c, e, G);
-      const T va = __shfl_sync(gmask, my_v, e, G);
-      const int cb = __shfl_sync(gmask, my_c, e + 1 < cnt ? e + 1 : e, G);
-      const T vb = e + 1 < cnt ? __shfl_sync(gmask, my_v, e + 1, G) : (T)0;
-      C xa[MAXCPL][NC], xb[MAXCPL][NC];
+    for (int e = 0; e < cnt; e += NB) {
+      int ci[NB];
+      T vi[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const bool ok = e + u < cnt;
+        ci[u] = __shfl_sync(gmask, my_c, ok ? e + u : e, G);
+        const T v = __shfl_sync(gmask, my_v, ok ? e + u : e, G);
+        vi[u] = ok ? v : (T)0;
+      }
+      C xs[NB][MAXCPL][NC];
 #pragma unroll
       for (int c = 0; c < MAXCPL; ++c)
         if (mask & (1u << c)) {
-          ld_chunk<NC>(X + (int64_t)ca * ldx_t + coff[c], xa[c]);
-          ld_chunk<NC>(X + (int64_t)cb * ldx_t + coff[c], xb[c]);
+#pragma unroll
+          for (int u = 0; u < NB; ++u)
+            ld_chunk<NC>(X + (int64_t)ci[u] * ldx_t + coff[c], xs[u][c]);
         }
 #pragma unroll
       for (int c = 0; c < MAXCPL; ++c)
         if (mask & (1u << c)) {
 #pragma unroll
-          for (int j = 0; j < NC; ++j) {
-            acc[c][j] = crfma<T>(va, xa[c][j], acc[c][j]);
-            acc[c][j] = crfma<T>(vb, xb[c][j], acc[c][j]);
-          }
+          for (int j = 0; j < NC; ++j)
+#pragma unroll
+            for (int u = 0; u < NB; ++u) acc[c][j] = crfma<T>(vi[u], xs[u][c][j], acc[c][j]);
         }
     }
   }
@@ -94,9 +104,9 @@ __device__ __forceinline__ void gather_row(const int32_t* __restrict__ colidx,
 
 // values-free gather for a unit-weight Laplacian's off-diagonal pattern:
 // acc[c][j] += sum_k X[col_k][chunk c] (weights all +1; the -1 sign and the
-// degree term are applied by the caller). Two entries in flight per step, a
-// missing second entry re-reads the first row with weight zero.
-template <typename T, int NC, int MAXCPL>
+// degree term are applied by the caller). Entries are taken NB per step as in
+// gather_row.
+template <typename T, int NC, int MAXCPL, int NB = 2>
 __device__ __forceinline__ void gather_row_vf(const int32_t* __restrict__ colidx, int k0, int k1,
                                               int row, int lg, int G, unsigned gmask,
                                               const T* __restrict__ X, int64_t ldx_t,
@@ -107,25 +117,33 @@ __device__ __forceinline__ void gather_row_vf(const int32_t* __restrict__ colidx
     const int kk = kb + lg;
     const int my_c = kk < k1 ? __ldg(colidx + kk) : row;
     const int cnt = min(G, k1 - kb);
-    for (int e = 0; e < cnt; e += 2) {
-      const int ca = __shfl_sync(gmask, my_c, e, G);
-      const int cb = __shfl_sync(gmask, my_c, e + 1 < cnt ? e + 1 : e, G);
-      const T vb = e + 1 < cnt ? (T)1 : (T)0;
-      C xa[MAXCPL][NC], xb[MAXCPL][NC];
+    for (int e = 0; e < cnt; e += NB) {
+      int ci[NB];
+      T vi[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const bool ok = e + u < cnt;
+        ci[u] = __shfl_sync(gmask, my_c, ok ? e + u : e, G);
+        vi[u] = ok ? (T)1 : (T)0;
+      }
+      C xs[NB][MAXCPL][NC];
 #pragma unroll
       for (int c = 0; c < MAXCPL; ++c)
         if (mask & (1u << c)) {
-          ld_chunk<NC>(X + (int64_t)ca * ldx_t + coff[c], xa[c]);
-          ld_chunk<NC>(X + (int64_t)cb * ldx_t + coff[c], xb[c]);
+#pragma unroll
+          for (int u = 0; u < NB; ++u)
+            ld_chunk<NC>(X + (int64_t)ci[u] * ldx_t + coff[c], xs[u][c]);
         }
 #pragma unroll
       for (int c = 0; c < MAXCPL; ++c)
         if (mask & (1u << c)) {
 #pragma unroll
           for (int j = 0; j < NC; ++j) {
-            acc[c][j].x += xa[c][j].x;
-            acc[c][j].y += xa[c][j].y;
-            acc[c][j] = crfma<T>(vb, xb[c][j], acc[c][j]);
+            // the first entry of a step always exists (e < cnt)
+            acc[c][j].x += xs[0][c][j].x;
+            acc[c][j].y += xs[0][c][j].y;
+#pragma unroll
+            for (int u = 1; u < NB; ++u) acc[c][j] = crfma<T>(vi[u], xs[u][c][j], acc[c][j]);
           }
         }
     }
@@ -246,12 +264,15 @@ __device__ __forceinline__ void cocg_dots_body(const CocgArgs<T>& a, const CocgA
       for (int c = 0; c < MAXCPL; ++c)
 #pragma unroll
         for (int j = 0; j < NC; ++j) acc[c][j] = mk<T>((T)0, (T)0);
+      // float kernels with at most 2 chunks per lane have the registers to
+      // keep 4 entries' loads in flight
+      constexpr int NB = (sizeof(T) == 4 && MAXCPL <= 2) ? 4 : 2;
       if constexpr (VF)
-        gather_row_vf<T, NC, MAXCPL>(a.lcolidx, k0, k1, (int)row, mp.lg, mp.G, gmask, R, ldt,
-                                     coff, mask, acc);
+        gather_row_vf<T, NC, MAXCPL, NB>(a.lcolidx, k0, k1, (int)row, mp.lg, mp.G, gmask, R,
+                                         ldt, coff, mask, acc);
       else
-        gather_row<T, NC, MAXCPL>(a.colidx, a.val, k0, k1, (int)row, mp.lg, mp.G, gmask, R, ldt,
-                                  coff, mask, acc);
+        gather_row<T, NC, MAXCPL, NB>(a.colidx, a.val, k0, k1, (int)row, mp.lg, mp.G, gmask, R,
+                                      ldt, coff, mask, acc);
       // values-free: L r = deg r - (sum over neighbours), deg = k1 - k0
       const T deg = (T)(k1 - k0);
 #pragma unroll
