@@ -468,10 +468,16 @@ __device__ __forceinline__ void ms_stream_stage(const CocgArgs<T>& a, unsigned c
   __syncthreads();
 }
 
-// elements e0, e0 + step, ... < e1 of the n x pairs element grid
+// elements of the range [lo, e1) of the n x pairs element grid: e0, e0 + step,
+// ...; with `down`, taken from the top of the range (element lo + e1 - 1 - e).
+// The dot kernel walks the rows upwards, so the w rows it wrote last are still
+// in L2 when a top-down update starts on them, and the r rows the update
+// writes last are the first ones the next dot kernel gathers. Elements are
+// independent, so the order changes only the cache reuse.
 template <typename T, int NS>
 __device__ __forceinline__ void ms_stream_elems(const CocgArgs<T>& a, const unsigned char* smem,
-                                                int64_t e0, int64_t e1, int64_t step) {
+                                                int64_t e0, int64_t e1, int64_t step,
+                                                int64_t lo, bool down) {
   using C = c2<T>;
   const int P = a.m0;
   const Coef<T>* scf = reinterpret_cast<const Coef<T>*>(smem);
@@ -484,8 +490,9 @@ __device__ __forceinline__ void ms_stream_elems(const CocgArgs<T>& a, const unsi
   const T* __restrict__ W = a.wbuf;
   T* __restrict__ S = a.sbuf;
   for (int64_t e = e0; e < e1; e += step) {
-    const int64_t row = e / P;
-    const int q = (int)(e - row * P);
+    const int64_t ee = down ? lo + e1 - 1 - e : e;
+    const int64_t row = ee / P;
+    const int q = (int)(ee - row * P);
     if (!sact[q]) continue;
     const int64_t off = (row * a.ldc + 2 * q) * 2;
     C rv[2], pv[2], wv[2], sv[2], rn[2];

@@ -257,7 +257,9 @@ __global__ void __launch_bounds__(THREADS)
     const int64_t chunk = (tot + b.gx - 1) / b.gx;
     const int64_t e0 = b.x * chunk;
     const int64_t e1 = e0 + chunk < tot ? e0 + chunk : tot;
-    ms_stream_elems<T, NS>(a, smem_raw, e0 + threadIdx.x, e1, blockDim.x);
+    // (bottom-up here: walking the items and elements top-down measured
+    // slower for the grouped launches)
+    ms_stream_elems<T, NS>(a, smem_raw, e0 + threadIdx.x, e1, blockDim.x, e0, false);
   }
 }
 

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(THREADS) k_ms_update_stream(CocgArgs<T> a) {
   extern __shared__ unsigned char smem_raw[];
   ms_stream_stage<T, NS>(a, smem_raw);
   ms_stream_elems<T, NS>(a, smem_raw, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                         a.n * (int64_t)a.m0, (int64_t)gridDim.x * blockDim.x);
+                         a.n * (int64_t)a.m0, (int64_t)gridDim.x * blockDim.x, 0, true);
 }
 
 template <typename T, int NS>
