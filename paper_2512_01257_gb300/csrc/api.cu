@@ -208,19 +208,38 @@ static void rayleigh_ritz_dev(Handle* h, const double* X, int m, int ld, double*
 // Z^T A Z = R^{-T} (X^T A X) R^{-1} = V diag(theta) V^T, and the Ritz vectors
 // are Z V = X (R^{-1} V), one tall product instead of two. Qout = X (R^{-1} V),
 // AQout = A Qout. ev_mid is recorded between the factorisations and the rest.
+// low_first (mixed precision): the first pass only preconditions X, so its
+// Gram is formed in float; X R1^{-1} is still an FP64 product, which keeps the
+// span of X. The pass is redone in FP64 when the float Gram needed a shift,
+// and an extra FP64 pass is added when the next Gram is not close to the
+// identity; the last factorisation is always FP64.
 // Returns the number of shifted passes.
 static int cholqr_rr(Handle* h, double*& X, double*& tmp, double* tmp2, int m, int ld,
-                     double* Qout, double* AQout, double* theta_d, cudaEvent_t ev_mid) {
+                     double* Qout, double* AQout, double* theta_d, cudaEvent_t ev_mid,
+                     bool low_first = false) {
   DenseWs d = dense_ws(h, m);
   int shifted = 0;
   int passes = 2;
+  bool low_used = false;
   for (int pass = 0; pass < passes; ++pass) {
-    gram(X, X, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true);
-    chol_inv(d.G, m, h->n, d.R, d.Rinv, d.status, h->stream);
-    h->launches += 3;
+    const bool low = low_first && pass == 0;
     int st = 0;
-    RF_CUDA(cudaMemcpyAsync(&st, d.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    RF_CUDA(cudaStreamSynchronize(h->stream));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const bool f32 = low && attempt == 0;
+      gram(X, X, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true, f32);
+      chol_inv(d.G, m, h->n, d.R, d.Rinv, d.status, h->stream, low_used && pass == 1);
+      h->launches += 3;
+      RF_CUDA(cudaMemcpyAsync(&st, d.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      RF_CUDA(cudaStreamSynchronize(h->stream));
+      if (f32 && st != 0) continue;  // the float Gram was not enough: FP64
+      low_used = f32;
+      break;
+    }
+    if (st & 4) {
+      // X R1^{-1} from the float pass is far from orthonormal: one more pass
+      st &= ~4;
+      if (passes < 4) ++passes;
+    }
     if (st == 2) throw Err{RAFEAST_ERR_CHOLESKY};
     if (st == 1) {
       ++shifted;
@@ -1305,7 +1324,8 @@ static bool solve_outer_tail(SolveRun& r) {
   const int m0 = r.m0, ldq = r.ldq;
   double* X = r.Qt;
   double* Y = r.T1;
-  r.shifted_total += cholqr_rr(h, X, Y, r.T2, m0, ldq, h->Q, h->AQ, h->theta_d, r.ev[4]);
+  r.shifted_total += cholqr_rr(h, X, Y, r.T2, m0, ldq, h->Q, h->AQ, h->theta_d, r.ev[4],
+                               r.prm.precision == RAFEAST_MIXED);
   residuals_host(h, h->Q, h->AQ, h->theta_d, m0, ldq, r.res);
   RF_CUDA(cudaEventRecord(r.ev[5], h->stream));
   h->theta.resize(m0);

@@ -326,17 +326,20 @@ void launch_from_internal(int64_t n, int m, const double* src, int ld, double* d
                           cudaStream_t s);
 // row-major tall blocks, FP64
 // G = X^T Y (m x m, ld m); sym: X^T Y is symmetric (X^T X, X^T A X), only
-// one triangle of tile blocks is formed and mirrored
+// one triangle of tile blocks is formed and mirrored; f32 (sym only): products
+// and per-CTA sums in float, for the preconditioning pass of a
+// mixed-precision Cholesky-QR
 void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
-          double* partial, int num_sms, cudaStream_t s, bool sym = false);
+          double* partial, int num_sms, cudaStream_t s, bool sym = false, bool f32 = false);
 // Y = X * M (M: m x mo, ld mo); upper: M is upper triangular (m == mo)
 void tall_gemm(const double* X, int64_t n, int m, int ldx, const double* M, int mo,
                double* Y, int ldy, cudaStream_t s, bool upper = false);
 // one-CTA Cholesky of G (+shift when needed) and inverse of the factor:
 // Rinv (m x m, ld m, upper) with Q R = X -> Q = X Rinv. status[0] = 0 ok,
-// 1 shifted, 2 failed; status[1..] unused.
+// 1 shifted, 2 failed; with check_id, bit 4 is added when an entry of G is
+// off the identity by more than 1/4. status[1..] unused.
 void chol_inv(double* G, int m, int64_t nrows, double* Rfac, double* Rinv, int* status,
-              cudaStream_t s);
+              cudaStream_t s, bool check_id = false);
 // one-CTA cyclic Jacobi: A (m x m, ld m, symmetric) -> eigenvalues ascending
 // in w, eigenvectors (columns) in V (m x m, ld m)
 // (work: 6 (m+1)^2 doubles; mixed-precision Jacobi, see kernels_dense.cu)

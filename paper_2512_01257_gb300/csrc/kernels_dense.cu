@@ -189,8 +189,11 @@ void launch_zero(void* p, size_t bytes, cudaStream_t s) {
 constexpr int GRAM_RB = 16;
 
 // SYM: the result is symmetric, so the 16-strided tile blocks below the
-// diagonal (u > v) are skipped; k_gram_sum mirrors them
-template <int U, bool SYM>
+// diagonal (u > v) are skipped; k_gram_sum mirrors them. A: the type the
+// products are formed and summed in within a CTA (double; float for the
+// preconditioning pass of a mixed-precision Cholesky-QR); the CTA partial
+// sums are added in double.
+template <int U, bool SYM, typename A = double>
 __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ X,
                                                       const double* __restrict__ Y, int64_t n,
                                                       int m, int ld, double* __restrict__ part) {
@@ -198,11 +201,11 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
   double* Xs = gsm;                 // [GRAM_RB][ld]
   double* Ys = gsm + GRAM_RB * ld;  // [GRAM_RB][ld]
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[U][U];
+  A acc[U][U];
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < U; ++v) acc[u][v] = (A)0;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = blockIdx.x * chunk;
   const int64_t r1 = min(n, r0 + chunk);
@@ -216,13 +219,13 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
     }
     __syncthreads();
     for (int rr = 0; rr < rows; ++rr) {
-      double xa[U], yb[U];
+      A xa[U], yb[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int a = tx + 16 * u;
-        xa[u] = a < m ? Xs[rr * ld + a] : 0.0;
+        xa[u] = a < m ? (A)Xs[rr * ld + a] : (A)0;
         const int b = ty + 16 * u;
-        yb[u] = b < m ? Ys[rr * ld + b] : 0.0;
+        yb[u] = b < m ? (A)Ys[rr * ld + b] : (A)0;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
 #pragma unroll
     for (int v = 0; v < U; ++v) {
       const int a = tx + 16 * u, b = ty + 16 * v;
-      if (a < m && b < m && (!SYM || u <= v)) out[a * m + b] = acc[u][v];
+      if (a < m && b < m && (!SYM || u <= v)) out[a * m + b] = (double)acc[u][v];
     }
 }
 
@@ -256,14 +259,14 @@ __global__ void k_gram_sum(const double* __restrict__ part, int nparts, int m, i
 
 int gram_parts(int num_sms) { return 2 * num_sms; }
 
-template <bool SYM>
+template <bool SYM, typename A = double>
 static void gram_partials(const double* X, const double* Y, int64_t n, int m, int ld,
                           double* partial, int parts, size_t smem, cudaStream_t s) {
   switch ((m + 15) / 16) {
-#define RF_GRAM(UU)                                                                   \
-  case UU:                                                                            \
-    ensure_dyn_smem(reinterpret_cast<const void*>(k_gram_partial<UU, SYM>), smem);   \
-    k_gram_partial<UU, SYM><<<parts, 256, smem, s>>>(X, Y, n, m, ld, partial);        \
+#define RF_GRAM(UU)                                                                      \
+  case UU:                                                                               \
+    ensure_dyn_smem(reinterpret_cast<const void*>(k_gram_partial<UU, SYM, A>), smem);   \
+    k_gram_partial<UU, SYM, A><<<parts, 256, smem, s>>>(X, Y, n, m, ld, partial);        \
     break;
     RF_GRAM(1) RF_GRAM(2) RF_GRAM(3) RF_GRAM(4) RF_GRAM(5) RF_GRAM(6) RF_GRAM(7) RF_GRAM(8)
 #undef RF_GRAM
@@ -272,11 +275,18 @@ static void gram_partials(const double* X, const double* Y, int64_t n, int m, in
 }
 
 void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
-          double* partial, int num_sms, cudaStream_t s, bool sym) {
+          double* partial, int num_sms, cudaStream_t s, bool sym, bool f32) {
   const int parts = gram_parts(num_sms);
   const size_t smem = 2 * GRAM_RB * (size_t)ld * sizeof(double);
-  if (sym) gram_partials<true>(X, Y, n, m, ld, partial, parts, smem, s);
-  else gram_partials<false>(X, Y, n, m, ld, partial, parts, smem, s);
+  if (f32) {
+    // only the symmetric X^T X of a preconditioning pass is formed in float
+    if (!sym) throw Err{RAFEAST_ERR_INVALID_ARG};
+    gram_partials<true, float>(X, Y, n, m, ld, partial, parts, smem, s);
+  } else if (sym) {
+    gram_partials<true>(X, Y, n, m, ld, partial, parts, smem, s);
+  } else {
+    gram_partials<false>(X, Y, n, m, ld, partial, parts, smem, s);
+  }
   RF_LAUNCH();
   k_gram_sum<<<(m * m + 255) / 256, 256, 0, s>>>(partial, parts, m, sym ? 1 : 0, G);
   RF_LAUNCH();
@@ -396,10 +406,19 @@ __device__ bool chol_inplace(double* S, int m) {
 }
 
 __global__ void k_chol_inv(const double* __restrict__ G, int m, double shift_scale,
-                           double* __restrict__ R, double* __restrict__ Rinv, int* status) {
+                           double* __restrict__ R, double* __restrict__ Rinv, int* status,
+                           int check_id) {
   extern __shared__ double S[];  // m*m
   __shared__ double s_shift;
-  for (int t = threadIdx.x; t < m * m; t += blockDim.x) S[t] = G[t];
+  __shared__ int s_far;
+  if (threadIdx.x == 0) s_far = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    S[t] = G[t];
+    // check_id: G is the Gram of a block that should be close to orthonormal;
+    // flag (status bit 4) when an entry is off the identity by more than 1/4
+    if (check_id && fabs(G[t] - ((t / m == t % m) ? 1.0 : 0.0)) > 0.25) s_far = 1;
+  }
   __syncthreads();
   int st = 0;
   bool ok = chol_inplace(S, m);
@@ -444,16 +463,16 @@ __global__ void k_chol_inv(const double* __restrict__ G, int m, double shift_sca
   }
   __syncthreads();
   // Rinv currently holds Linv^T stored as Rinv[j][i] = Linv[i][j] = (Linv^T)[j][i]
-  if (threadIdx.x == 0) status[0] = st;
+  if (threadIdx.x == 0) status[0] = st | (s_far ? 4 : 0);
 }
 
 void chol_inv(double* G, int m, int64_t nrows, double* Rfac, double* Rinv, int* status,
-              cudaStream_t s) {
+              cudaStream_t s, bool check_id) {
   const size_t smem = (size_t)m * m * sizeof(double);
   ensure_dyn_smem(reinterpret_cast<const void*>(k_chol_inv), smem);
   const double u = DBL_EPSILON / 2;
   const double scale = 11.0 * ((double)nrows * m + (double)m * (m + 1)) * u;
-  k_chol_inv<<<1, 256, smem, s>>>(G, m, scale, Rfac, Rinv, status);
+  k_chol_inv<<<1, 256, smem, s>>>(G, m, scale, Rfac, Rinv, status, check_id ? 1 : 0);
   RF_LAUNCH();
 }
 
