@@ -141,23 +141,38 @@ static DenseWs dense_ws(Handle* h, int m) {
 }
 
 // X (n x m, ld) <- X R^{-1}; returns number of shifted passes; R_total (host,
-// m x m row-major upper) accumulates the factor if non-null.
-static int cholqr(Handle* h, double*& X, double*& tmp, int m, int ld, std::vector<double>* Rtot) {
+// m x m row-major upper) accumulates the factor if non-null. low_first: the
+// first pass forms its Gram in float, as in cholqr_rr below (the pass only
+// preconditions; the products with R^{-1} stay FP64 and the last pass is FP64).
+static int cholqr(Handle* h, double*& X, double*& tmp, int m, int ld, std::vector<double>* Rtot,
+                  bool low_first = false) {
   DenseWs d = dense_ws(h, m);
   int shifted = 0;
   int passes = 2;
+  bool low_used = false;
   std::vector<double> Racc;
   if (Rtot) {
     Racc.assign((size_t)m * m, 0.0);
     for (int i = 0; i < m; ++i) Racc[i * m + i] = 1.0;
   }
   for (int pass = 0; pass < passes; ++pass) {
-    gram(X, X, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true);
-    chol_inv(d.G, m, h->n, d.R, d.Rinv, d.status, h->stream);
-    h->launches += 3;
+    const bool low = low_first && pass == 0;
     int st = 0;
-    RF_CUDA(cudaMemcpyAsync(&st, d.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    RF_CUDA(cudaStreamSynchronize(h->stream));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const bool f32 = low && attempt == 0;
+      gram(X, X, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true, f32);
+      chol_inv(d.G, m, h->n, d.R, d.Rinv, d.status, h->stream, low_used && pass == 1);
+      h->launches += 3;
+      RF_CUDA(cudaMemcpyAsync(&st, d.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      RF_CUDA(cudaStreamSynchronize(h->stream));
+      if (f32 && st != 0) continue;  // the float Gram was not enough: FP64
+      low_used = f32;
+      break;
+    }
+    if (st & 4) {
+      st &= ~4;
+      if (passes < 4) ++passes;
+    }
     if (st == 2) throw Err{RAFEAST_ERR_CHOLESKY};
     if (st == 1) {
       ++shifted;
@@ -2050,7 +2065,7 @@ int rafeast_warmstart(rafeast_t hh, double lmin, double lmax, int m0, int p, int
   h->launches += 3;
   h->spmm_launches += 1;
   for (int it = 0; it < q; ++it) {
-    cholqr(h, Y, Z, k, ld, nullptr);
+    cholqr(h, Y, Z, k, ld, nullptr, true);
     launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, k, ld, sL, sI, Y, Z,
                              h->num_sms, h->stream);
     launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, k, ld, sL, sI, Z, Y,
@@ -2058,7 +2073,7 @@ int rafeast_warmstart(rafeast_t hh, double lmin, double lmax, int m0, int p, int
     h->launches += 2;
     h->spmm_launches += 2;
   }
-  cholqr(h, Y, Z, k, ld, nullptr);
+  cholqr(h, Y, Z, k, ld, nullptr, true);
   // Rayleigh-Ritz on the m0+p columns: A_Y = Y^T A Y, eigh, and only the m0
   // Ritz vectors kept are formed (Q = Y V_sel, then A Q)
   double* AY = (double*)scratch(h, S_AQ2, sizeof(double) * h->n * ld);
