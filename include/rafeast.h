@@ -59,7 +59,10 @@ extern "C" {
 /* ---- enums --------------------------------------------------------------- */
 #define RAFEAST_FP64 0   /* every step in double                              */
 #define RAFEAST_MIXED 1  /* shifted solves + their SpMM in float32; Gram,      *
-                          * Cholesky-QR, Rayleigh-Ritz, residuals in double    */
+                          * Cholesky-QR, Rayleigh-Ritz, residuals in double    *
+                          * (the Gram of the first, preconditioning Cholesky-  *
+                          * QR pass is summed in float; its products with the  *
+                          * factor and the last pass stay double)              */
 
 #define RAFEAST_FORM_DIRECT 0     /* COCG right-hand side Q (as printed)      */
 #define RAFEAST_FORM_CORRECTION 1 /* COCG right-hand side A Q - Q diag(theta); *
@@ -314,7 +317,10 @@ int rafeast_rayleigh_ritz(rafeast_t h, int m, double* Q, double* theta,
  * Omega (n x (m0+p)) from seed, Y = B^(2q+1) Omega with B the affine map of
  * RAFEAST_OPT_WARMSTART_MAP, Q = orth(Y), then Rayleigh-Ritz on A keeps the
  * m0 Ritz vectors whose Ritz values are closest to (lmin+lmax)/2. The result
- * becomes the handle's subspace (used by RAFEAST_START_SUBSPACE). */
+ * becomes the handle's subspace (used by RAFEAST_START_SUBSPACE). Y is
+ * re-orthonormalised after each pair of products; each orthonormalisation is
+ * a Cholesky-QR whose first, preconditioning pass sums its Gram in float
+ * (products with the factor and the last pass in double). */
 int rafeast_warmstart(rafeast_t h, double lmin, double lmax, int m0, int p,
                       int q, uint64_t seed);
 
