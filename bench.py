@@ -548,6 +548,22 @@ print(json.dumps(dict(t_ws=t_ws, t_step=t_step, t_rr=t_rr, nnz=a.nnz)))
     return {"est": est, "sample": sample}
 
 
+def _unit_laplacian(lap):
+    """(values-free, off-diagonal count): whether the CSR is a unit-weight
+    graph Laplacian (off-diagonal entries -1, diagonal = the row's number of
+    off-diagonal entries), the matrices whose dot kernels gather on the
+    pattern alone."""
+    import numpy as np
+    n = lap.n
+    rp = lap.row_ptr.astype(np.int64)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    diag = rows == lap.col_idx
+    off = ~diag
+    deg = np.bincount(rows[off], minlength=n)
+    vf = bool(np.all(lap.values[off] == -1.0) and np.all(lap.values[diag] == deg[rows[diag]]))
+    return vf, int(off.sum())
+
+
 def _fp64_dots_roofline(hbm, prof, lap, dev):
     """The FP64 seed dot kernel is bound by the FP64 pipe, not by HBM: every
     gathered real entry costs one FP64 add (values-free) or FMA, 1.25 TFLOP/s
@@ -557,17 +573,9 @@ def _fp64_dots_roofline(hbm, prof, lap, dev):
     w = z r - L r, the five dot products). The active pairs come from the
     library's byte count of the same launches (A once plus, per pair, r read
     and w written)."""
-    import numpy as np
     import torch
     n = lap.n
-    rp = lap.row_ptr.astype(np.int64)
-    rows = np.repeat(np.arange(n), np.diff(rp))
-    diag = rows == lap.col_idx
-    off = ~diag
-    deg = np.diff(rp) - np.bincount(rows[diag], minlength=n)
-    vf = bool(np.all(lap.values[off] == -1.0)
-              and np.all(lap.values[diag] == deg[rows[diag]]))
-    nnz_off = int(off.sum())
+    vf, nnz_off = _unit_laplacian(lap)
     abytes = (nnz_off * 4.0 if vf else lap.nnz * 12.0) + 4.0 * (n + 1)
     pairb = n * 2 * 2.0 * 8.0
     launches = max(prof["dots_launches"], 1.0)
