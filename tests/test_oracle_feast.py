@@ -195,3 +195,43 @@ def test_rafeast_correction_reaches_tight_tol_with_relaxed_solves():
     assert r.status == F.STATUS_OK and r.m_found == k
     assert M.eig_relerr(r.evals, lam[:k]) < 1e-11
     assert M.sin_theta(r.evecs, v[:, :k]) < 1e-8
+
+
+def test_one_norm_hand_computed():
+    """||A||_1 is the largest column sum of absolute values (the convergence
+    test's normalisation, Algorithm 1's "until convergence" as read here).
+    The matrices separate it from the row-sum, Frobenius and spectral norms
+    and from a sum without absolute values."""
+    # path Laplacian P5: column sums of |a_ij| are 2, 4, 4, 4, 2
+    a = G.path(5).scipy()
+    assert F.one_norm(a) == 4.0
+    # ||A||_2 = 2 - 2 cos(4 pi / 5) = 3.618..., ||A||_F = sqrt(22)
+    assert abs(np.linalg.norm(a.toarray(), 2) - (2 - 2 * np.cos(4 * np.pi / 5))) < 1e-12
+    # a diagonal shift adds to every column sum
+    assert F.one_norm(G.path(5, shift=0.5).scipy()) == 4.5
+    # columns (1, 7), rows (6, 2): the 1-norm is 7, the infinity-norm 6
+    assert F.one_norm(sp.csr_matrix(np.array([[1.0, 5.0], [0.0, 2.0]]))) == 7.0
+    # negative entries count by their size: |.| column sums (5, 2), plain (-1, 0)
+    assert F.one_norm(sp.csr_matrix(np.array([[-3.0, 1.0], [2.0, -1.0]]))) == 5.0
+
+
+def test_residuals_hand_computed():
+    """res_i = ||A q_i - lam_i q_i||_2 / ||A||_1, worked by hand on the path
+    Laplacian P5 (||A||_1 = 4):
+    * q = e_0, lam = 1: A e_0 - e_0 = (0, -1, 0, 0, 0), res = 1/4;
+    * q = e_2, lam = 2: A e_2 - 2 e_2 = (0, -1, 0, -1, 0), res = sqrt(2)/4
+      (a max-norm would give 1/4, a 1-norm 2/4);
+    * q = e_2, lam = 0: (0, -1, 2, -1, 0), res = sqrt(6)/4;
+    * q = (1,...,1)/sqrt(5), lam = 0.5: A q = 0, res = 0.5/4.
+    With a shift of 0.5 every column sum grows by 0.5 and A e_0 = 1.5 e_0 - e_1."""
+    a = G.path(5).scipy()
+    e = np.eye(5)
+    q = np.stack([e[0], e[2], e[2], np.ones(5) / np.sqrt(5)], axis=1)
+    lam = np.array([1.0, 2.0, 0.0, 0.5])
+    expect = np.array([1.0, np.sqrt(2.0), np.sqrt(6.0), 0.5]) / 4.0
+    assert np.allclose(F.residuals(a, lam, q), expect, rtol=0, atol=1e-15)
+    # the same with A Q and ||A||_1 passed in
+    assert np.allclose(F.residuals(a, lam, q, aq=a @ q, norm_a=4.0), expect, rtol=0, atol=1e-15)
+    s = G.path(5, shift=0.5).scipy()
+    got = F.residuals(s, np.array([1.5, 0.0]), np.stack([e[0], e[0]], axis=1))
+    assert np.allclose(got, np.array([1.0, np.sqrt(1.5 ** 2 + 1.0)]) / 4.5, rtol=0, atol=1e-15)
