@@ -74,8 +74,11 @@ extern "C" {
 #define RAFEAST_START_SUBSPACE 1 /* the handle's subspace (warmstart / set)   */
 
 #define RAFEAST_CREATE_NO_REORDER 1u      /* keep the caller's row order      */
-#define RAFEAST_CREATE_FORCE_REORDER 2u   /* always apply the RCM order       */
+#define RAFEAST_CREATE_FORCE_REORDER 2u   /* always apply the reordering      */
 #define RAFEAST_CREATE_CHECK_SYMMETRY 4u  /* O(nnz) host check, -2 on failure */
+#define RAFEAST_CREATE_RCM 8u             /* reverse Cuthill-McKee instead of *
+                                           * the default recursive breadth-   *
+                                           * first bisection                  */
 
 /* option keys for rafeast_set_option */
 #define RAFEAST_OPT_WARMSTART_MAP 1 /* 0 auto, 1 literal (A-lmin)/(lmax-lmin), *
@@ -114,6 +117,17 @@ extern "C" {
                                      * its off-diagonal pattern alone, with   *
                                      * L r = deg r - sum of neighbours; 1:    *
                                      * always read the values                 */
+#define RAFEAST_OPT_TILED 14        /* seed dot kernel of the multi-shift    *
+                                     * float32 solve with the streamed update: *
+                                     * 0 (default) tiled (row tiles whose      *
+                                     * gathered rows are staged in shared      *
+                                     * memory) when the matrix has tiles, the  *
+                                     * autotuner choosing between it and the   *
+                                     * register gathers; 1 register gathers    *
+                                     * only; 2 tiled only (when it has tiles)  */
+#define RAFEAST_OPT_TILE_CB 15      /* with RAFEAST_OPT_TILED = 2: column     *
+                                     * pairs per block of the tiled dot kernel *
+                                     * (4 or 8; 0 = autotuned)                 */
 #define RAFEAST_OPT_TEST_STALL 9    /* test hook: bytes (multiple of 16) that  *
                                      * every bulk-copy stage waits for and no *
                                      * copy delivers, so the bounded wait     *
@@ -218,8 +232,9 @@ int rafeast_profile(rafeast_t h, int reset, double* out);
 int rafeast_profile_history(rafeast_t h, int max_len, int* active_cols, double* max_relres,
                             double* kernel_ms);
 
-/* Matrix facts: n, internal reorder flag (1 when rows are permuted), ||A||_1
- * and the Gershgorin interval of A. Any output pointer may be NULL. */
+/* Matrix facts: n, internal row order (0 the caller's, 1 recursive
+ * breadth-first bisection, 2 reverse Cuthill-McKee), ||A||_1 and the
+ * Gershgorin interval of A. Any output pointer may be NULL. */
 int rafeast_matrix_info(rafeast_t h, int64_t* n, int* reordered,
                         double* norm1, double* gersh_lo, double* gersh_hi);
 
@@ -298,11 +313,17 @@ int rafeast_gram(rafeast_t h, int m, const double* X, const double* Y, double* G
  *   (larger m returns -1 and rafeast_last_error says why). stream: a
  *   cudaStream_t on the current device; the call only enqueues work, G is
  *   ready when the stream reaches it.
- *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) and caches it; make that first call before any
- *   stream capture begins. All calls share the array: calls whose work
- *   overlaps on the GPU (other streams, other threads) race on it and must be
- *   serialised by the caller. */
+ *   The first call on a device sets up: it looks up the array's device
+ *   address (cudaGetSymbolAddress) and caches it. CUDA loads modules lazily
+ *   by default, so that first call is also the one that loads the array and
+ *   the entry point's kernels onto the device, about 2 MiB plus code: it
+ *   allocates, later calls do not. Make the first call (n = 1, m = 1 will do)
+ *   before reserving device memory for another allocator and before any
+ *   stream capture begins; no cudaDeviceReset may follow it. An error that
+ *   was already pending when the call begins is returned as -3 and left
+ *   pending. All calls share the array: calls whose work overlaps on the GPU
+ *   (other streams, other threads) race on it and must be serialised by the
+ *   caller. */
 int rafeast_gram_noalloc(const double* X, const double* Y, int64_t n, int m, double* G,
                          void* stream);
 

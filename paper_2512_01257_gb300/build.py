@@ -4,7 +4,7 @@ Each translation unit is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and linked into
 ``paper_2512_01257_gb300/librafeast.so`` against the shared CUDA runtime.
 
-    python -m paper_2512_01257_gb300.build [--verbose] [--extra FLAG ...]
+    python -m paper_2512_01257_gb300.build [--verbose] [NVCC_FLAG ...]
 """
 from __future__ import annotations
 
@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librafeast.so")
 SOURCES = ["kernels_sparse.cu", "kernels_batched.cu", "kernels_tma.cu", "kernels_dense.cu",
-           "api.cu", "noalloc.cu", "hostmath.cpp"]
+           "kernels_tiled.cu", "api.cu", "noalloc.cu", "hostmath.cpp", "tiling.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -66,11 +66,11 @@ def build(verbose: bool = False, extra=()) -> str:
 
 
 def main(argv=None):
-    ap = argparse.ArgumentParser()
+    ap = argparse.ArgumentParser(
+        epilog="Any other argument (e.g. -DNAME=VALUE) is passed to nvcc for every unit.")
     ap.add_argument("--verbose", action="store_true")
-    ap.add_argument("--extra", nargs="*", default=[])
-    a = ap.parse_args(argv)
-    print(build(a.verbose, a.extra))
+    a, extra = ap.parse_known_args(argv)
+    print(build(a.verbose, extra))
 
 
 if __name__ == "__main__":

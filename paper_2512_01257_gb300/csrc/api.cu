@@ -284,8 +284,8 @@ static int cholqr_rr(Handle* h, double*& X, double*& tmp, double* tmp2, int m, i
 static void residuals_host(Handle* h, const double* Q, const double* AQ, const double* theta_d,
                            int m, int ld, std::vector<double>& res) {
   DenseWs d = dense_ws(h, m);
-  col_resid2(Q, AQ, theta_d, h->n, m, ld, d.small, h->stream);
-  h->launches += 1;
+  col_resid2(Q, AQ, theta_d, h->n, m, ld, d.small, d.part, h->num_sms, h->stream);
+  h->launches += 2;
   res.resize(m);
   RF_CUDA(cudaMemcpyAsync(res.data(), d.small, sizeof(double) * m, cudaMemcpyDeviceToHost,
                           h->stream));
@@ -736,10 +736,44 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
   std::vector<float> tk;  // per executed step: dot ms, update ms (profiling)
   CocgCtl ctl;
   memset(&ctl, 0, sizeof(ctl));
+  // tiled seed dot kernel (float32, streamed update, the matrix has tiles):
+  // the tile arrays and the per-CTA sums; tl_for(cb) describes the launch
+  // with cb column pairs per block
+  const bool vf = a.lcolidx != nullptr;
+  const bool can_tile = !fp64 && stream && h->ntiles > 0 && h->opt_tiled != 1 &&
+                        (vf ? h->llidx != nullptr : h->lidx != nullptr);
+  double* tpart = can_tile ? (double*)scratch(h, S_TPART, sizeof(double) * (size_t)h->num_sms *
+                                                             TILE_MAX_OCC * 16 * 10)
+                           : nullptr;
+  auto tl_for = [&](int cb) {
+    TileArgs tl;
+    tl.ntiles = h->ntiles;
+    tl.max_union = h->tile_max_union;
+    tl.trow = h->trow;
+    tl.uoff = h->uoff;
+    tl.ucol = h->ucol;
+    tl.uself = h->uself;
+    tl.lidx = vf ? h->llidx : h->lidx;
+    tl.cb = cb;
+    tl.ncb = (pairs + cb - 1) / cb;
+    tl.part = tpart;
+    return tl;
+  };
+  int dot_cb = 0, dot_occ = 0;  // tiled dot kernel shape in use (dot_cb = 0: register gathers)
+  auto launch_dots = [&](const CocgArgs<T>& ad, int buf, int cb, int occ) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (cb > 0) {
+        launch_ms_dots_tiled(ad, tl_for(cb), h->num_sms, occ, h->stream);
+        return;
+      }
+    }
+    launch_cocg_dots<T>(ad, 2, buf, h->num_sms, h->stream);
+  };
   // capture `steps` COCG steps with the given shapes; event nodes around each
   // kernel when timing is wanted (the graph records them on every replay)
   auto capture = [&](const CocgArgs<T>& ad, const CocgArgs<T>& au, int steps, bool timed,
-                     std::vector<cudaEvent_t>& evs, cudaGraphExec_t& exec) {
+                     std::vector<cudaEvent_t>& evs, cudaGraphExec_t& exec, int cb = 0,
+                     int occ = 0) {
     if (timed) {
       evs.resize(2 * steps + 1);
       for (auto& e : evs) RF_CUDA(cudaEventCreate(&e));
@@ -751,7 +785,7 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
       for (int it = 0; it < steps; ++it) {
         if (timed)
           RF_CUDA(cudaEventRecordWithFlags(evs[2 * it], h->stream, cudaEventRecordExternal));
-        launch_cocg_dots<T>(ad, 2, it & 1, h->num_sms, h->stream);
+        launch_dots(ad, it & 1, cb, occ);
         if (timed)
           RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], h->stream, cudaEventRecordExternal));
         if (stream) launch_ms_update_stream<T>(au, h->num_sms, h->stream);
@@ -802,9 +836,14 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
       au.lanes = kv.second.ul;
       au.cpl = kv.second.uc;
       au.occ = kv.second.um;
-      have = true;
+      dot_cb = can_tile ? kv.second.dt : 0;
+      dot_occ = kv.second.dt ? kv.second.dm : 0;
+      if (h->opt_tiled == 2 && can_tile && dot_cb == 0) have = false;  // retune
+      else have = true;
     }
-  if (!have && h->opt_autotune && !h->opt_lanes && !h->opt_cpl) {
+  const bool tune = h->opt_autotune && !h->opt_lanes && !h->opt_cpl;
+  if (!have && !tune && can_tile && h->opt_tiled == 2) dot_cb = 8;
+  if (!have && tune) {
     // (lanes, chunks, CTAs per SM; 0 = the default instance)
     // (the last three only for FP64, whose one-chunk dot instance runs at
     // 3 CTAs per SM)
@@ -851,22 +890,50 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
         au.occ = c[2];
       }
     }
+    // tiled dot kernel: column pairs per block x CTAs per SM (0: as many as
+    // fit); only the dot kernel's time counts, the update is the streamed one
+    if (can_tile) {
+      const int tcand[][2] = {{8, 0}, {4, 0}, {8, 2}, {4, 4}};
+      for (const auto& c : tcand) {
+        if (ctl.done) break;
+        if (c[0] > 2 * pairs && c[0] > 4) continue;  // mostly empty blocks
+        std::vector<cudaEvent_t> evs;
+        cudaGraphExec_t exec = nullptr;
+        capture(au, au, 2, true, evs, exec, c[0], c[1]);
+        std::vector<float> times;
+        replay(exec, 2, true, evs, &times);
+        RF_CUDA(cudaGraphExecDestroy(exec));
+        for (auto& e : evs) RF_CUDA(cudaEventDestroy(e));
+        tk.insert(tk.end(), times.begin(), times.end());
+        const float td = std::min(times[0], times[2]);
+        if (td < best_d || (h->opt_tiled == 2 && dot_cb == 0)) {
+          best_d = td;
+          dot_cb = c[0];
+          dot_occ = c[1];
+        }
+      }
+    }
     Handle::Shape shp;
     shp.dl = ad.lanes;
     shp.dc = ad.cpl;
-    shp.dm = ad.occ;
+    shp.dm = dot_cb ? dot_occ : ad.occ;
     shp.ul = au.lanes;
     shp.uc = au.cpl;
     shp.um = au.occ;
+    shp.dt = dot_cb;
     h->tuned.push_back(std::make_pair(key, shp));
   }
-  h->prof[6] = ad.occ * 10000 + ad.lanes * 100 + ad.cpl;
+  if (can_tile && h->opt_tiled == 2 && h->opt_tile_cb > 0) {
+    dot_cb = h->opt_tile_cb;  // forced block width (tests)
+    dot_occ = 0;
+  }
+  h->prof[6] = dot_cb ? 1000000 + dot_cb * 100 + dot_occ : ad.occ * 10000 + ad.lanes * 100 + ad.cpl;
   h->prof[7] = au.occ * 10000 + au.lanes * 100 + au.cpl;
   int chunk = std::max(2, h->opt_chunk);
   chunk += chunk & 1;
   std::vector<cudaEvent_t> evs;
   cudaGraphExec_t exec = nullptr;
-  capture(ad, au, chunk, prof, evs, exec);
+  capture(ad, au, chunk, prof, evs, exec, dot_cb, dot_occ);
   const int max_replays = (prm.max_inner + 2) / chunk + 2;
   int replays = 0;
   for (; replays < max_replays && !ctl.done; ++replays) {
@@ -1313,7 +1380,11 @@ static void solve_begin(SolveRun& r, Handle* h, const rafeast_params& prm) {
                              h->AQ, h->num_sms, h->stream);
     h->launches += 1;
     h->spmm_launches += 1;
-    col_dot(h->Q, h->AQ, h->n, m0, h->ldq, h->theta_d, h->stream);
+    {
+      DenseWs d = dense_ws(h, m0);
+      col_dot(h->Q, h->AQ, h->n, m0, h->ldq, h->theta_d, d.part, h->num_sms, h->stream);
+      h->launches += 2;
+    }
     h->theta.resize(m0);
     RF_CUDA(cudaMemcpyAsync(h->theta.data(), h->theta_d, sizeof(double) * m0,
                             cudaMemcpyDeviceToHost, h->stream));
@@ -1558,14 +1629,44 @@ int rafeast_create(rafeast_t* out, int64_t n, int64_t nnz, const int32_t* row_pt
     h->norm1 = norm1 > 0.0 ? norm1 : 1.0;
     h->glo = glo;
     h->ghi = ghi;
-    // row order: reverse Cuthill-McKee when it narrows the band
+    // row order. Default: recursive breadth-first bisection when its row
+    // tiles gather from at least 15% fewer rows than the caller's order
+    // (tiling.cpp); RAFEAST_CREATE_RCM: reverse Cuthill-McKee when it
+    // narrows the band by 30%; FORCE_REORDER applies the chosen kind always
     std::vector<int32_t> perm;
     bool reorder = false;
     if (!(flags & RAFEAST_CREATE_NO_REORDER) && n > 1) {
-      rcm_order(n, rp.data(), ci.data(), perm);
-      const int64_t bw0 = bandwidth(n, rp.data(), ci.data(), nullptr);
-      const int64_t bw1 = bandwidth(n, rp.data(), ci.data(), perm.data());
-      reorder = (flags & RAFEAST_CREATE_FORCE_REORDER) || (double)bw1 < 0.7 * (double)bw0;
+      if (flags & RAFEAST_CREATE_RCM) {
+        rcm_order(n, rp.data(), ci.data(), perm);
+        const int64_t bw0 = bandwidth(n, rp.data(), ci.data(), nullptr);
+        const int64_t bw1 = bandwidth(n, rp.data(), ci.data(), perm.data());
+        reorder = (flags & RAFEAST_CREATE_FORCE_REORDER) || (double)bw1 < 0.7 * (double)bw0;
+        h->order_kind = reorder ? 2 : 0;
+      } else {
+        bisect_order(n, rp.data(), ci.data(), 32, perm);
+        bool better = (flags & RAFEAST_CREATE_FORCE_REORDER) != 0;
+        if (!better) {
+          TileHost t0, t1;
+          const bool ok0 = build_tiles(n, rp.data(), ci.data(), TILE_UCAP, TILE_TMAX, TILE_NNZCAP, t0);
+          // the permuted pattern (indices only) for the comparison
+          std::vector<int32_t> ip(n), prp(n + 1), pci(nnz);
+          for (int64_t r = 0; r < n; ++r) ip[perm[r]] = (int32_t)r;
+          prp[0] = 0;
+          for (int64_t r = 0; r < n; ++r) {
+            const int32_t o = perm[r];
+            int32_t* dst = pci.data() + prp[r];
+            int c = 0;
+            for (int32_t k = rp[o]; k < rp[o + 1]; ++k) dst[c++] = ip[ci[k]];
+            prp[r + 1] = prp[r] + c;
+          }
+          const bool ok1 = build_tiles(n, prp.data(), pci.data(), TILE_UCAP, TILE_TMAX, TILE_NNZCAP, t1);
+          const double u0 = ok0 ? (double)t0.ucol.size() : 1e300;
+          const double u1 = ok1 ? (double)t1.ucol.size() : 1e300;
+          better = ok1 && u1 < 0.85 * u0;
+        }
+        reorder = better;
+        h->order_kind = reorder ? 1 : 0;
+      }
     }
     std::vector<int32_t> rp2 = rp, ci2 = ci;
     std::vector<double> va2 = va;
@@ -1631,6 +1732,49 @@ int rafeast_create(rafeast_t* out, int64_t n, int64_t nnz, const int32_t* row_pt
         RF_CUDA(cudaMemcpy(h->lcolidx, lci.data(), sizeof(int32_t) * h->nnz_off,
                            cudaMemcpyHostToDevice));
     }
+    // row tiles of the tiled dot kernel, on the internal order
+    {
+      TileHost t;
+      if (nnz > 0 && build_tiles(n, rp2.data(), ci2.data(), TILE_UCAP, TILE_TMAX, TILE_NNZCAP, t)) {
+        std::vector<uint16_t> lx, llx;
+        std::vector<int32_t> us;
+        tile_local_index(n, rp2.data(), ci2.data(), t, lx, us);
+        h->ntiles = (int)t.trow.size() - 1;
+        h->tile_max_union = t.max_union;
+        h->tile_max_rows = t.max_rows;
+        h->tile_ratio = (double)t.ucol.size() / (double)n;
+        RF_CUDA(cudaMalloc(&h->trow, sizeof(int32_t) * t.trow.size()));
+        RF_CUDA(cudaMalloc(&h->uoff, sizeof(int32_t) * t.uoff.size()));
+        RF_CUDA(cudaMalloc(&h->ucol, sizeof(int32_t) * t.ucol.size()));
+        RF_CUDA(cudaMalloc(&h->uself, sizeof(int32_t) * us.size()));
+        RF_CUDA(cudaMalloc(&h->lidx, sizeof(uint16_t) * lx.size()));
+        RF_CUDA(cudaMemcpy(h->trow, t.trow.data(), sizeof(int32_t) * t.trow.size(),
+                           cudaMemcpyHostToDevice));
+        RF_CUDA(cudaMemcpy(h->uoff, t.uoff.data(), sizeof(int32_t) * t.uoff.size(),
+                           cudaMemcpyHostToDevice));
+        RF_CUDA(cudaMemcpy(h->ucol, t.ucol.data(), sizeof(int32_t) * t.ucol.size(),
+                           cudaMemcpyHostToDevice));
+        RF_CUDA(cudaMemcpy(h->uself, us.data(), sizeof(int32_t) * us.size(),
+                           cudaMemcpyHostToDevice));
+        RF_CUDA(cudaMemcpy(h->lidx, lx.data(), sizeof(uint16_t) * lx.size(),
+                           cudaMemcpyHostToDevice));
+        if (unit && h->nnz_off > 0) {
+          // the off-diagonal pattern gathers from the same unions
+          std::vector<int32_t> lrp(n + 1), lci;
+          lci.reserve(h->nnz_off);
+          lrp[0] = 0;
+          for (int64_t r = 0; r < n; ++r) {
+            for (int32_t k = rp2[r]; k < rp2[r + 1]; ++k)
+              if (ci2[k] != r) lci.push_back(ci2[k]);
+            lrp[r + 1] = (int32_t)lci.size();
+          }
+          tile_local_index(n, lrp.data(), lci.data(), t, llx, us);
+          RF_CUDA(cudaMalloc(&h->llidx, sizeof(uint16_t) * llx.size()));
+          RF_CUDA(cudaMemcpy(h->llidx, llx.data(), sizeof(uint16_t) * llx.size(),
+                             cudaMemcpyHostToDevice));
+        }
+      }
+    }
     std::vector<float> v32(nnz);
     for (int64_t k = 0; k < nnz; ++k) v32[k] = (float)va2[k];
     RF_CUDA(cudaMalloc(&h->rowptr, sizeof(int32_t) * (n + 1)));
@@ -1662,8 +1806,9 @@ void rafeast_destroy(rafeast_t hh) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& b : h->bufs)
     if (b.p) cudaFree(b.p);
-  void* ptrs[] = {h->rowptr, h->colidx, h->val64,   h->val32,  h->perm,   h->iperm,
-                  h->Q,      h->AQ,     h->theta_d, h->lrowptr, h->lcolidx};
+  void* ptrs[] = {h->rowptr, h->colidx, h->val64,   h->val32,   h->perm,  h->iperm,
+                  h->Q,      h->AQ,     h->theta_d, h->lrowptr, h->lcolidx, h->trow,
+                  h->uoff,   h->ucol,   h->uself,   h->lidx,    h->llidx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -1715,6 +1860,14 @@ int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
       if (value < 0 || value > 1) return RAFEAST_ERR_INVALID_ARG;
       h->opt_values_free = (int)value;
       return RAFEAST_OK;
+    case RAFEAST_OPT_TILED:
+      if (value < 0 || value > 2) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_tiled = (int)value;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_TILE_CB:
+      if (value != 0 && value != 4 && value != 8) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_tile_cb = (int)value;
+      return RAFEAST_OK;
     case RAFEAST_OPT_CPL:
       if (value < 0 || value > 16) return RAFEAST_ERR_INVALID_ARG;
       h->opt_cpl = (int)value;
@@ -1763,7 +1916,7 @@ int rafeast_matrix_info(rafeast_t hh, int64_t* n, int* reordered, double* norm1,
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return RAFEAST_ERR_INVALID_ARG;
   if (n) *n = h->n;
-  if (reordered) *reordered = h->reordered ? 1 : 0;
+  if (reordered) *reordered = h->reordered ? h->order_kind : 0;
   if (norm1) *norm1 = h->norm1;
   if (glo) *glo = h->glo;
   if (ghi) *ghi = h->ghi;
@@ -1918,11 +2071,11 @@ int rafeast_filter(rafeast_t hh, const rafeast_params* prm, const double* Q, con
     // Rayleigh quotients q_i^T A q_i / q_i^T q_i
     std::vector<double> num(m0), den(m0);
     DenseWs d = dense_ws(h, m0);
-    col_dot(Qi, AQi, h->n, m0, ldq, d.small, h->stream);
+    col_dot(Qi, AQi, h->n, m0, ldq, d.small, d.part, h->num_sms, h->stream);
     RF_CUDA(cudaMemcpyAsync(num.data(), d.small, sizeof(double) * m0, cudaMemcpyDeviceToHost,
                             h->stream));
     RF_CUDA(cudaStreamSynchronize(h->stream));
-    col_dot(Qi, Qi, h->n, m0, ldq, d.small, h->stream);
+    col_dot(Qi, Qi, h->n, m0, ldq, d.small, d.part, h->num_sms, h->stream);
     RF_CUDA(cudaMemcpyAsync(den.data(), d.small, sizeof(double) * m0, cudaMemcpyDeviceToHost,
                             h->stream));
     RF_CUDA(cudaStreamSynchronize(h->stream));

@@ -134,35 +134,32 @@ __device__ void cocg_scalar_step(const CocgArgs<T>& a, int NC) {
   }
 }
 
-// Scalar step of the multi-shift COCG (last CTA of the seed's dot kernel).
-// The seed system M_s = z_s I - A runs the same Chronopoulos-Gear recurrence
-// as above (systems = columns i; the dot kernel treated column pairs as the
-// two "shifts" of a chunk). Every other shift j, M_j = M_s + sigma_j I with
-// sigma_j = z_j - z_s, shares the seed's Krylov space: its residual is
-// zeta_k^j r_k, with (three-term residual-polynomial recurrence of CG at
-// t = -sigma_j)
-//   zeta_{k+1} = zeta_k zeta_{k-1} a_{k-1}
-//                / (zeta_{k-1} a_{k-1} (1 + sigma a_k) + a_k b_{k-1} (zeta_{k-1} - zeta_k)),
-//   alpha_k^j = a_k zeta_{k+1} / zeta_k,  beta_{k-1}^j = b_{k-1} (zeta_k / zeta_{k-1})^2,
-// where a_k, b_{k-1} are the seed's alpha_k and beta_{k-1}. A shifted system
-// stops when |zeta_k|^2 nu_k <= tol^2 ||b||^2; a column keeps iterating (the
-// seed recurrence keeps running) while any of its shifts does.
+// counters of one multi-shift scalar step (shared memory of the CTA that
+// runs it, or combined over several CTAs)
+struct MsCount {
+  int active, brk, cap, mx, mn, cols;
+  double worst;
+};
+
+__device__ inline void ms_count_init(MsCount& c) {
+  c.active = 0;
+  c.brk = 0;
+  c.cap = 0;
+  c.mx = 0;
+  c.mn = 0x7fffffff;
+  c.cols = 0;
+  c.worst = 0.0;
+}
+
+// per-column part of the multi-shift scalar step for columns [c0, c1) at
+// step k; counters into cnt (shared), the largest nu/||b||^2 of an active
+// system into *worst (per thread). Columns are independent of one another.
 template <typename T>
-__device__ void ms_scalar_step(const CocgArgs<T>& a) {
-  __shared__ int s_active, s_brk, s_cap, s_max, s_min;
-  if (threadIdx.x == 0) {
-    s_active = 0;
-    s_brk = 0;
-    s_cap = 0;
-    s_max = 0;
-    s_min = 0x7fffffff;
-  }
-  __syncthreads();
-  const int k = __ldcg(&a.ctl->iter);
-  const int ncol = a.m0 * 2;  // columns (pairs x 2)
+__device__ void ms_scalar_cols(const CocgArgs<T>& a, int k, int c0, int c1, MsCount& cnt,
+                               double* worst_out) {
   const int ns = a.ns;
   double worst = 0.0;
-  for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
+  for (int i = c0 + (int)threadIdx.x; i < c1; i += blockDim.x) {
     SysState st = a.st[i];
     double* acc = a.acc + 5 * i;
     const double gre = __ldcg(acc + 0), gim = __ldcg(acc + 1);
@@ -199,14 +196,14 @@ __device__ void ms_scalar_step(const CocgArgs<T>& a) {
       bool seed_running = st.iters < 0 || k == 0;
       if (seed_running && (nu <= thr || k >= a.max_inner || !seed_ok)) {
         if (!(nu <= thr)) {
-          if (!seed_ok) atomicAdd(&s_brk, 1);
-          else atomicAdd(&s_cap, 1);
+          if (!seed_ok) atomicAdd(&cnt.brk, 1);
+          else atomicAdd(&cnt.cap, 1);
         }
         st.iters = k;
         seed_running = false;
         if (st.bnorm2 > 0.0) {
-          atomicMax(&s_max, k);
-          atomicMin(&s_min, k);
+          atomicMax(&cnt.mx, k);
+          atomicMin(&cnt.mn, k);
         }
       } else if (seed_running) {
         st.iters = -1;
@@ -226,14 +223,14 @@ __device__ void ms_scalar_step(const CocgArgs<T>& a) {
           const double nuj = (zr * zr + zi * zi) * nu;
           if (nuj <= thr || k >= a.max_inner || !seed_ok) {
             if (!(nuj <= thr)) {
-              if (!seed_ok) atomicAdd(&s_brk, 1);
-              else atomicAdd(&s_cap, 1);
+              if (!seed_ok) atomicAdd(&cnt.brk, 1);
+              else atomicAdd(&cnt.cap, 1);
             }
             ss.active = 0;
             ss.iters = k;
             if (st.bnorm2 > 0.0) {
-              atomicMax(&s_max, k);
-              atomicMin(&s_min, k);
+              atomicMax(&cnt.mx, k);
+              atomicMin(&cnt.mn, k);
             }
           } else {
             // zeta_{k+1}
@@ -263,7 +260,7 @@ __device__ void ms_scalar_step(const CocgArgs<T>& a) {
                 !(zp2 > 1e-300)) {
               ss.active = 0;
               ss.iters = k;
-              atomicAdd(&s_brk, 1);
+              atomicAdd(&cnt.brk, 1);
             } else {
               // alpha_k^j = a_k zeta_{k+1} / zeta_k
               const double qr = (znr * zc.x + zni * zc.y) / zc2, qi = (zni * zc.x - znr * zc.y) / zc2;
@@ -295,7 +292,7 @@ __device__ void ms_scalar_step(const CocgArgs<T>& a) {
         cf.alpha = mk<T>((T)are, (T)aim);
         cf.ca = seed_running ? mk<T>((T)(cq.x * are - cq.y * aim), (T)(cq.x * aim + cq.y * are))
                              : mk<T>((T)0, (T)0);
-        atomicAdd(&s_active, 1);
+        atomicAdd(&cnt.active, 1);
       } else {
         st.active = 0;
         column_on = false;
@@ -319,45 +316,90 @@ __device__ void ms_scalar_step(const CocgArgs<T>& a) {
     a.st[i] = st;
     a.cf[i] = cf;
   }
-  __syncthreads();
-  __shared__ int s_cols;
-  if (threadIdx.x == 0) s_cols = 0;
-  __syncthreads();
-  for (int q = threadIdx.x; q < a.m0; q += blockDim.x) {
+  *worst_out = worst;
+}
+
+// column activity of the pairs [p0, p1) after their columns' step; counts
+// the active pairs into cnt.cols
+template <typename T>
+__device__ void ms_colact(const CocgArgs<T>& a, int p0, int p1, MsCount& cnt) {
+  for (int q = p0 + (int)threadIdx.x; q < p1; q += blockDim.x) {
     const int any = a.st[2 * q].active | a.st[2 * q + 1].active;
     a.colact[q] = any;
-    if (any) atomicAdd(&s_cols, 1);
+    if (any) atomicAdd(&cnt.cols, 1);
   }
-  __syncthreads();
-  if (a.hist) {
-    __shared__ double s_worst[32];
-    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, 16));
-    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, 8));
-    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, 4));
-    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, 2));
-    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, 1));
-    if ((threadIdx.x & 31) == 0) s_worst[threadIdx.x >> 5] = worst;
-    __syncthreads();
-    if (threadIdx.x == 0 && k <= a.max_inner) {
-      double w = 0.0;
-      for (int t = 0; t < (int)(blockDim.x >> 5); ++t) w = fmax(w, s_worst[t]);
-      a.hist[k] = s_cols;
-      a.rhist[k] = sqrt(w);
-    }
-  }
+}
+
+// block-wide maximum of a per-thread value (every thread gets it)
+__device__ inline double block_max(double v) {
+  __shared__ double s_w[32];
+  __shared__ double s_r;
+  v = fmax(v, __shfl_xor_sync(0xffffffffu, v, 16));
+  v = fmax(v, __shfl_xor_sync(0xffffffffu, v, 8));
+  v = fmax(v, __shfl_xor_sync(0xffffffffu, v, 4));
+  v = fmax(v, __shfl_xor_sync(0xffffffffu, v, 2));
+  v = fmax(v, __shfl_xor_sync(0xffffffffu, v, 1));
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    CocgCtl* c = a.ctl;
-    c->active = s_active;
-    c->breakdown += s_brk;
-    c->capped += s_cap;
-    if (s_max > c->max_iters) c->max_iters = s_max;
-    if (s_min != 0x7fffffff && (c->min_iters == 0 || s_min < c->min_iters)) c->min_iters = s_min;
-    c->iter = k + 1;
-    if (s_active == 0) c->done = 1;
-    __threadfence();
-    c->ticket = 0;
+    double w = 0.0;
+    for (int t = 0; t < (int)(blockDim.x >> 5); ++t) w = fmax(w, s_w[t]);
+    s_r = w;
   }
+  __syncthreads();
+  return s_r;
+}
+
+// the end of a multi-shift step (thread 0): profile history, statistics,
+// the step counter, the done flag, the dot kernel's ticket
+template <typename T>
+__device__ void ms_scalar_finish(const CocgArgs<T>& a, int k, const MsCount& cnt) {
+  CocgCtl* c = a.ctl;
+  if (a.hist && k <= a.max_inner) {
+    a.hist[k] = cnt.cols;
+    a.rhist[k] = sqrt(cnt.worst);
+  }
+  c->active = cnt.active;
+  c->breakdown += cnt.brk;
+  c->capped += cnt.cap;
+  if (cnt.mx > c->max_iters) c->max_iters = cnt.mx;
+  if (cnt.mn != 0x7fffffff && (c->min_iters == 0 || cnt.mn < c->min_iters)) c->min_iters = cnt.mn;
+  c->iter = k + 1;
+  if (cnt.active == 0) c->done = 1;
+  __threadfence();
+  c->ticket = 0;
+}
+
+// Scalar step of the multi-shift COCG (last CTA of the seed's dot kernel).
+// The seed system M_s = z_s I - A runs the same Chronopoulos-Gear recurrence
+// as above (systems = columns i; the dot kernel treated column pairs as the
+// two "shifts" of a chunk). Every other shift j, M_j = M_s + sigma_j I with
+// sigma_j = z_j - z_s, shares the seed's Krylov space: its residual is
+// zeta_k^j r_k, with (three-term residual-polynomial recurrence of CG at
+// t = -sigma_j)
+//   zeta_{k+1} = zeta_k zeta_{k-1} a_{k-1}
+//                / (zeta_{k-1} a_{k-1} (1 + sigma a_k) + a_k b_{k-1} (zeta_{k-1} - zeta_k)),
+//   alpha_k^j = a_k zeta_{k+1} / zeta_k,  beta_{k-1}^j = b_{k-1} (zeta_k / zeta_{k-1})^2,
+// where a_k, b_{k-1} are the seed's alpha_k and beta_{k-1}. A shifted system
+// stops when |zeta_k|^2 nu_k <= tol^2 ||b||^2; a column keeps iterating (the
+// seed recurrence keeps running) while any of its shifts does.
+template <typename T>
+__device__ void ms_scalar_step(const CocgArgs<T>& a) {
+  __shared__ MsCount cnt;
+  if (threadIdx.x == 0) ms_count_init(cnt);
+  __syncthreads();
+  const int k = __ldcg(&a.ctl->iter);
+  double worst = 0.0;
+  ms_scalar_cols<T>(a, k, 0, 2 * a.m0, cnt, &worst);
+  __syncthreads();
+  ms_colact<T>(a, 0, a.m0, cnt);
+  __syncthreads();
+  if (a.hist) {
+    const double w = block_max(worst);
+    if (threadIdx.x == 0) cnt.worst = w;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ms_scalar_finish<T>(a, k, cnt);
 }
 
 }  // namespace rafeast

@@ -50,6 +50,14 @@ struct CocgCtl {
   int max_iters;        // most iterations taken by any system
   int min_iters;        // fewest iterations taken by a system with b != 0
   int timeout;          // a bounded device wait ran out
+  // tiled dot kernel: CTAs of each column block that have finished, column
+  // blocks whose scalar step is done, and the step's counters summed over
+  // the column blocks (all zero between steps)
+  unsigned int cbticket[16];
+  unsigned int ticket2;
+  int g_active, g_brk, g_cap, g_mx, g_cols;
+  int g_mn;                     // 0x7fffffff between steps
+  unsigned long long g_worst;   // bits of a non-negative double
 };
 
 // per-system scalar state, double precision (one struct per system s)
@@ -144,6 +152,35 @@ template <typename T> struct CocgArgs {
   const int32_t* lcolidx;
 };
 
+// ---- row tiles of the tiled sparse products (tiling.cpp, kernels_tiled.cu) ----
+// Tile t holds rows [trow[t], trow[t+1]); its union (the rows its nonzeros
+// name and its own rows, ascending) is ucol[uoff[t] .. uoff[t+1]); its first
+// row sits at union position uself[t]; every nonzero has its column's
+// position in its tile's union in lidx (parallel to the CSR column array).
+struct TileHost {
+  std::vector<int32_t> trow, uoff, ucol;
+  int max_union = 0, max_rows = 0;
+};
+struct TileArgs {
+  int ntiles;
+  int max_union;
+  const int32_t* trow;
+  const int32_t* uoff;
+  const int32_t* ucol;
+  const int32_t* uself;
+  const uint16_t* lidx;  // for the pattern the kernel gathers on
+  int cb;                // column pairs per block (4 or 8)
+  int ncb;               // column blocks
+  double* part;          // [grid * cb * 10]: per-CTA sums
+};
+#ifndef RF_TILE_UCAP
+#define RF_TILE_UCAP 512
+#endif
+constexpr int TILE_UCAP = RF_TILE_UCAP;  // most union rows of a tile
+constexpr int TILE_TMAX = 256;    // most rows of a tile
+constexpr int TILE_NNZCAP = 3072; // most nonzeros of a tile (full CSR)
+constexpr int TILE_MAX_OCC = 8;   // most resident CTAs per SM of the tiled kernel
+
 // ---- handle -----------------------------------------------------------------
 struct DevBuf {
   void* p = nullptr;
@@ -166,6 +203,18 @@ struct Handle {
   int32_t* lrowptr = nullptr;
   int32_t* lcolidx = nullptr;
   int64_t nnz_off = 0;
+  // row tiles (ntiles = 0 when the matrix has a row that gathers from more
+  // than TILE_UCAP rows): union arrays, and the local indices of the full
+  // CSR and of the off-diagonal pattern
+  int ntiles = 0, tile_max_union = 0, tile_max_rows = 0;
+  int32_t* trow = nullptr;
+  int32_t* uoff = nullptr;
+  int32_t* ucol = nullptr;
+  int32_t* uself = nullptr;
+  uint16_t* lidx = nullptr;
+  uint16_t* llidx = nullptr;
+  double tile_ratio = 0.0;  // sum of union sizes / n
+  int order_kind = 0;       // 0 caller's order, 1 bisection, 2 reverse Cuthill-McKee
   double shift = 0.0;
   double norm1 = 0.0, glo = 0.0, ghi = 0.0;
   bool reordered = false;
@@ -186,11 +235,14 @@ struct Handle {
   int opt_solver = 1;  // 0: COCG per shift, 1: multi-shift COCG (default)
   int opt_update = 0;  // multi-shift update: 0 auto, 1 gathered products, 2 streamed
   int opt_values_free = 0;  // 0: values-free gathers for unit Laplacians, 1: never
+  int opt_tiled = 0;        // seed dot kernel: 0 auto (tiled when built), 1 never, 2 only tiled
+  int opt_tile_cb = 0;      // tiled dot kernel: forced column pairs per block (0: autotuned)
   // autotuned kernel shapes (lanes, chunks per lane) of the multi-shift
   // kernels, keyed by (pairs, shifts, precision)
   struct Shape {
     int dl, dc, ul, uc;
     int dm = 0, um = 0;  // forced CTAs per SM (0: default instance)
+    int dt = 0;          // tiled dot kernel: column pairs per block (0: register gathers)
   };
   std::vector<std::pair<int64_t, Shape>> tuned;
   int opt_profile = 0;
@@ -217,7 +269,7 @@ void* scratch(Handle* h, int slot, size_t bytes);  // keep-alive buffer per slot
 void ensure_dyn_smem(const void* fn, size_t bytes);
 enum Slot {
   S_STATE = 0, S_DACC, S_QT, S_TMP1, S_TMP2, S_SCAL, S_GRAM, S_SMALL, S_OMEGA,
-  S_AQ2, S_IO1, S_IO2, S_BATCH, S_COUNT
+  S_AQ2, S_IO1, S_IO2, S_BATCH, S_TPART, S_COUNT
 };
 
 // ---- host math (hostmath.cpp) ------------------------------------------------
@@ -230,6 +282,23 @@ void rcm_order(int64_t n, const int32_t* rowptr, const int32_t* colidx,
                std::vector<int32_t>& perm);
 int64_t bandwidth(int64_t n, const int32_t* rowptr, const int32_t* colidx,
                   const int32_t* perm /* may be null */);
+// recursive breadth-first bisection of a symmetric pattern: perm[new] = old
+void bisect_order(int64_t n, const int32_t* rowptr, const int32_t* colidx, int leaf,
+                  std::vector<int32_t>& perm);
+// row tiles with unions of at most ucap rows, at most tmax rows and at most
+// nnzcap nonzeros; false when a single row exceeds a cap
+bool build_tiles(int64_t n, const int32_t* rowptr, const int32_t* colidx, int ucap, int tmax,
+                 int nnzcap, TileHost& t);
+// union positions of every nonzero of a pattern whose columns lie in the
+// tiles' unions (the full CSR or its off-diagonal part); uself per tile.
+// lidx gets 8 zero entries of padding after the last nonzero.
+void tile_local_index(int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                      const TileHost& t, std::vector<uint16_t>& lidx,
+                      std::vector<int32_t>& uself);
+// tiled seed dot kernel of the multi-shift COCG (float32, streamed update);
+// occ_cap: most CTAs per SM (0: as many as fit, at most TILE_MAX_OCC)
+void launch_ms_dots_tiled(const CocgArgs<float>& a, const TileArgs& tl, int num_sms,
+                          int occ_cap, cudaStream_t s);
 
 // ---- kernel launchers (kernels_sparse.cu) --------------------------------------
 int nc_pad(int nc);  // shifts rounded up to a compiled NC (1, 2, 4, 8)
@@ -348,18 +417,19 @@ void chol_inv(double* G, int m, int64_t nrows, double* Rfac, double* Rinv, int* 
 void small_gemm(const double* A, int ta, const double* B, int tb, double* C, int m, double alpha,
                 double gamma, cudaStream_t s);
 void jacobi_eigh(double* A, int m, double* w, double* V, double* work, cudaStream_t s);
-// res_i = ||AQ_i - theta_i Q_i||^2 (sums, m), FP64
+// res_i = ||AQ_i - theta_i Q_i||^2 (sums, m), FP64; part: workspace of
+// 2 * num_sms * m doubles (per-block sums, added in a fixed order)
 void col_resid2(const double* Q, const double* AQ, const double* theta, int64_t n, int m,
-                int ld, double* out, cudaStream_t s);
+                int ld, double* out, double* part, int num_sms, cudaStream_t s);
 // Qt = f_i * Q + D (D in T, ld ldd)
 template <typename T>
 void launch_combine(const double* Q, int ldq, const T* D, int ldd, const double* f,
                     int64_t n, int m, double* Qt, cudaStream_t s);
 void launch_zero(void* p, size_t bytes, cudaStream_t s);
 void launch_widen(const float* src, double* dst, int64_t count, cudaStream_t s);
-// out[i] = sum_r X[r][i] Y[r][i]
+// out[i] = sum_r X[r][i] Y[r][i] (part as for col_resid2)
 void col_dot(const double* X, const double* Y, int64_t n, int m, int ld, double* out,
-             cudaStream_t s);
+             double* part, int num_sms, cudaStream_t s);
 void launch_cast_to_f32(const double* src, float* dst, int64_t count, cudaStream_t s);
 
 }  // namespace rafeast

@@ -499,6 +499,7 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
   __shared__ T cs[64 * 2];  // c, s per pair (me/2 <= 64)
   __shared__ int pq[64 * 2];
   __shared__ double s_off, s_tot;
+  __shared__ double s_woff[32], s_wtot[32];  // per-warp sums, added in warp order
   __shared__ int s_order[128];
   __shared__ int s_rot;
   const T tiny = sizeof(T) == 4 ? (T)1e-37 : (T)1e-300;
@@ -527,8 +528,18 @@ __global__ void k_jacobi(const double* __restrict__ Ain, int m, double* __restri
     off = warp_sum(off);
     tot = warp_sum(tot);
     if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&s_off, off);
-      atomicAdd(&s_tot, tot);
+      s_woff[threadIdx.x >> 5] = off;
+      s_wtot[threadIdx.x >> 5] = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double so = 0.0, st = 0.0;
+      for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
+        so += s_woff[wi];
+        st += s_wtot[wi];
+      }
+      s_off = so;
+      s_tot = st;
     }
     __syncthreads();
     if (!(s_off > off_tol * s_tot) || s_tot == 0.0) break;
@@ -685,10 +696,13 @@ void jacobi_eigh(double* A, int m, double* w, double* V, double* work, cudaStrea
 // ---------------------------------------------------------------------------
 // column reductions over rows
 // mode 0: out[i] = sum_r X[r][i] Y[r][i];  mode 1: out[i] = sum_r (Y - th_i X)^2
+// Block b sums the rows b, b + B, b + 2B, ... of every column into part[b];
+// a second kernel adds the B partial sums of each column in increasing b, so
+// the result does not depend on the order in which blocks run.
 // ---------------------------------------------------------------------------
 __global__ void k_colred(const double* __restrict__ X, const double* __restrict__ Y,
                          const double* __restrict__ th, int64_t n, int m, int ld, int mode,
-                         double* out) {
+                         double* part) {
   const int i = threadIdx.x;
   if (i >= m) return;
   const double t = mode ? th[i] : 0.0;
@@ -702,25 +716,35 @@ __global__ void k_colred(const double* __restrict__ X, const double* __restrict_
       acc = fma(x, y, acc);
     }
   }
-  atomicAdd(out + i, acc);
+  part[(int64_t)blockIdx.x * m + i] = acc;
+}
+
+__global__ void k_colsum(const double* __restrict__ part, int nparts, int m, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int b = 0; b < nparts; ++b) s += part[(int64_t)b * m + i];
+  out[i] = s;
+}
+
+static void colred(const double* X, const double* Y, const double* th, int64_t n, int m, int ld,
+                   int mode, double* out, double* part, int num_sms, cudaStream_t s) {
+  const int threads = ((m + 31) / 32) * 32;
+  const int blocks = (int)std::min<int64_t>(n, 2 * (int64_t)num_sms);
+  k_colred<<<blocks, threads, 0, s>>>(X, Y, th, n, m, ld, mode, part);
+  RF_LAUNCH();
+  k_colsum<<<(m + 127) / 128, 128, 0, s>>>(part, blocks, m, out);
+  RF_LAUNCH();
 }
 
 void col_dot(const double* X, const double* Y, int64_t n, int m, int ld, double* out,
-             cudaStream_t s) {
-  RF_CUDA(cudaMemsetAsync(out, 0, m * sizeof(double), s));
-  const int threads = ((m + 31) / 32) * 32;
-  int blocks = (int)std::min<int64_t>(n, 1024);
-  k_colred<<<blocks, threads, 0, s>>>(X, Y, nullptr, n, m, ld, 0, out);
-  RF_LAUNCH();
+             double* part, int num_sms, cudaStream_t s) {
+  colred(X, Y, nullptr, n, m, ld, 0, out, part, num_sms, s);
 }
 
 void col_resid2(const double* Q, const double* AQ, const double* theta, int64_t n, int m, int ld,
-                double* out, cudaStream_t s) {
-  RF_CUDA(cudaMemsetAsync(out, 0, m * sizeof(double), s));
-  const int threads = ((m + 31) / 32) * 32;
-  int blocks = (int)std::min<int64_t>(n, 1024);
-  k_colred<<<blocks, threads, 0, s>>>(Q, AQ, theta, n, m, ld, theta ? 1 : 0, out);
-  RF_LAUNCH();
+                double* out, double* part, int num_sms, cudaStream_t s) {
+  colred(Q, AQ, theta, n, m, ld, theta ? 1 : 0, out, part, num_sms, s);
 }
 
 // ---------------------------------------------------------------------------

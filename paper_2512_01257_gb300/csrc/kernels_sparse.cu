@@ -79,7 +79,8 @@ __global__ void k_cocg_reset(CocgArgs<T> a, int NC) {
     if (s % NC == 0) a.colact[s / NC] = 1;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    CocgCtl c;
+    CocgCtl c = {};
+    c.g_mn = 0x7fffffff;
     c.ticket = 0;
     c.iter = 0;
     c.active = nsys;
@@ -228,7 +229,8 @@ __global__ void k_ms_reset(CocgArgs<T> a) {
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    CocgCtl c;
+    CocgCtl c = {};
+    c.g_mn = 0x7fffffff;
     c.ticket = 0;
     c.iter = 0;
     c.active = ncol;

@@ -3,10 +3,21 @@
 // Same result as rafeast_gram, for callers that must not have the library
 // allocate device memory during the call. Its scratch (one m x m partial sum
 // per CTA) lives in a file-scope device array of fixed size, compiled into
-// the library: every GPU that loads the library holds those 2 MiB until the
-// process exits. Host code never passes the array's symbol to a kernel (on
-// the host the symbol is only a stand-in, not a device address); the device
-// address is looked up once per device with cudaGetSymbolAddress and cached.
+// the library. Host code never passes the array's symbol to a kernel (on the
+// host the symbol is only a stand-in, not a device address); the device
+// address is looked up once per device with cudaGetSymbolAddress, with that
+// device current, and cached.
+//
+// The array belongs to this file's module. CUDA loads modules lazily by
+// default (CUDA_MODULE_LOADING=LAZY), so the first call on a device is the one
+// that loads the module: that call allocates the 2 MiB array and the code of
+// the entry point's kernels on the device (it has all of them loaded), and
+// later calls allocate nothing. From then on the
+// device holds the array until the process exits. A caller that reserves
+// device memory for its own allocator, or captures streams, makes a first call
+// (n = 1, m = 1 is enough) before doing so. The cached address is only valid
+// for the device context it was looked up in: no cudaDeviceReset may come
+// after the first call on that device.
 //
 // Calls share the array, so two calls whose kernels overlap on the GPU (two
 // streams, or two host threads) race on it. Each call overwrites every
@@ -23,23 +34,6 @@ constexpr int NOALLOC_PARTS = 64;   // most per-CTA partial sums
 constexpr size_t NOALLOC_DOUBLES = (size_t)NOALLOC_PARTS * NOALLOC_MAX_M * NOALLOC_MAX_M;
 
 static __device__ __align__(256) double g_noalloc_partials[NOALLOC_DOUBLES];  // 2 MiB
-
-static std::mutex g_noalloc_mu;
-static double* g_noalloc_addr[128] = {nullptr};
-
-// device address of the array on device `dev` (set up on first use)
-static cudaError_t noalloc_scratch(int dev, double** out) {
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess) return e;
-    g_noalloc_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_addr[dev];
-  return cudaSuccess;
-}
 
 constexpr int NA_RB = 16;  // rows staged per step
 
@@ -104,6 +98,37 @@ __global__ void k_gram_sum_noalloc(const double* __restrict__ part, int nparts, 
   }
 }
 
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_addr[128] = {nullptr};
+
+// device address of the array on device `dev`, the current device. The first
+// call there sets up: it looks the address up (which loads this file's
+// module, allocating the array) and has every kernel of the entry point
+// loaded, so that all of the device memory the entry point ever takes is
+// taken by that first call.
+static cudaError_t noalloc_scratch(int dev, double** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    const void* fns[5] = {reinterpret_cast<const void*>(k_gram_partial_noalloc<1>),
+                          reinterpret_cast<const void*>(k_gram_partial_noalloc<2>),
+                          reinterpret_cast<const void*>(k_gram_partial_noalloc<3>),
+                          reinterpret_cast<const void*>(k_gram_partial_noalloc<4>),
+                          reinterpret_cast<const void*>(k_gram_sum_noalloc)};
+    for (const void* f : fns) {
+      e = cudaFuncGetAttributes(&fa, f);
+      if (e != cudaSuccess) return e;
+    }
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
 }  // namespace rafeast
 
 using namespace rafeast;
@@ -121,9 +146,16 @@ extern "C" int rafeast_gram_noalloc(const double* X, const double* Y, int64_t n,
     set_last_message(msg);
     return RAFEAST_ERR_INVALID_ARG;
   }
-  cudaGetLastError();  // a stale error of an earlier call is not ours
+  // an error left pending by the caller's own earlier work is reported as
+  // it is and left pending for the caller (not cleared, not launched over)
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    set_last_error(e, "rafeast_gram_noalloc: a CUDA error was pending before the call",
+                   __FILE__, __LINE__);
+    return RAFEAST_ERR_CUDA;
+  }
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   double* part = nullptr;
   if (e == cudaSuccess) e = noalloc_scratch(dev, &part);
   if (e != cudaSuccess) {

@@ -40,6 +40,7 @@ RAFEAST_START_SUBSPACE = 1
 RAFEAST_CREATE_NO_REORDER = 1
 RAFEAST_CREATE_FORCE_REORDER = 2
 RAFEAST_CREATE_CHECK_SYMMETRY = 4
+RAFEAST_CREATE_RCM = 8
 RAFEAST_OPT_WARMSTART_MAP = 1
 RAFEAST_OPT_CHUNK = 2
 RAFEAST_OPT_AUTOTUNE = 3
@@ -53,6 +54,8 @@ RAFEAST_OPT_CPL = 10
 RAFEAST_OPT_SOLVER = 11
 RAFEAST_OPT_UPDATE = 12
 RAFEAST_OPT_VALUES_FREE = 13
+RAFEAST_OPT_TILED = 14
+RAFEAST_OPT_TILE_CB = 15
 
 EXPORTS = [
     "rafeast_create", "rafeast_destroy", "rafeast_status_string", "rafeast_set_option",
@@ -250,8 +253,8 @@ def rafeast_matrix_info(h):
     n, r, n1, lo, hi = C.c_int64(), C.c_int(), C.c_double(), C.c_double(), C.c_double()
     _check(load().rafeast_matrix_info(h, C.byref(n), C.byref(r), C.byref(n1), C.byref(lo),
                                       C.byref(hi)), "rafeast_matrix_info")
-    return dict(n=n.value, reordered=bool(r.value), norm1=n1.value, gersh_lo=lo.value,
-                gersh_hi=hi.value)
+    return dict(n=n.value, reordered=bool(r.value), order=int(r.value), norm1=n1.value,
+                gersh_lo=lo.value, gersh_hi=hi.value)
 
 
 def rafeast_quadrature(lmin, lmax, nc, e=1.0):
