@@ -289,6 +289,10 @@ void bisect_order(int64_t n, const int32_t* rowptr, const int32_t* colidx, int l
 // nnzcap nonzeros; false when a single row exceeds a cap
 bool build_tiles(int64_t n, const int32_t* rowptr, const int32_t* colidx, int ucap, int tmax,
                  int nnzcap, TileHost& t);
+// union rows per row of the tiles of a few evenly spaced row windows (an
+// estimate of the whole pattern's ratio; -1 when a row exceeds a cap)
+double tile_union_ratio(int64_t n, const int32_t* rowptr, const int32_t* colidx, int ucap,
+                        int tmax, int nnzcap, int windows);
 // union positions of every nonzero of a pattern whose columns lie in the
 // tiles' unions (the full CSR or its off-diagonal part); uself per tile.
 // lidx gets 8 zero entries of padding after the last nonzero.

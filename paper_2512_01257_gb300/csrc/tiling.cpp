@@ -131,36 +131,61 @@ void bisect_order(int64_t n, const int32_t* rp, const int32_t* ci, int leaf,
   bisect_rec(c, std::move(all), 0, 0, 0);
 }
 
-bool build_tiles(int64_t n, const int32_t* rp, const int32_t* ci, int ucap, int tmax,
-                 int nnzcap, TileHost& t) {
-  t.trow.assign(1, 0);
-  t.uoff.assign(1, 0);
-  t.ucol.clear();
-  t.max_union = 0;
-  t.max_rows = 0;
-  std::vector<int32_t> stamp(n, -1);
+namespace {
+
+// set of int32 keys of the current tile's union (open addressing, linear
+// probing); cleared by resetting the slots it filled
+struct USet {
+  std::vector<int32_t> slot;
+  std::vector<int32_t> used;
+  unsigned mask;
+  explicit USet(int cap) {
+    unsigned c = 1;
+    while (c < 4u * (unsigned)cap) c <<= 1;
+    slot.assign(c, -1);
+    mask = c - 1;
+  }
+  bool insert(int32_t k) {  // true when k was not in the set
+    unsigned h = ((unsigned)k * 2654435761u) & mask;
+    while (slot[h] != -1) {
+      if (slot[h] == k) return false;
+      h = (h + 1) & mask;
+    }
+    slot[h] = k;
+    used.push_back((int32_t)h);
+    return true;
+  }
+  void erase_last(size_t count) {  // undo the last `count` insertions
+    for (size_t i = 0; i < count; ++i) {
+      slot[used.back()] = -1;
+      used.pop_back();
+    }
+  }
+  void clear() {
+    for (int32_t h : used) slot[h] = -1;
+    used.clear();
+  }
+};
+
+// greedy tiles of rows [lo, hi): appends row ends, union sizes and sorted
+// unions; false when one row exceeds a cap
+bool tiles_range(int64_t lo, int64_t hi, const int32_t* rp, const int32_t* ci, int ucap,
+                 int tmax, int nnzcap, std::vector<int32_t>& ends, std::vector<int32_t>& sizes,
+                 std::vector<int32_t>& ucol) {
+  USet set(ucap);
   std::vector<int32_t> cur, added;
-  cur.reserve(ucap);
-  int32_t tid = 0;
-  int64_t r = 0;
-  while (r < n) {
+  int64_t r = lo;
+  while (r < hi) {
     const int64_t t0 = r;
     cur.clear();
-    while (r < n && r - t0 < tmax && (int64_t)rp[r + 1] - rp[t0] <= nnzcap) {
+    set.clear();
+    while (r < hi && r - t0 < tmax && (int64_t)rp[r + 1] - rp[t0] <= nnzcap) {
       added.clear();
-      if (stamp[r] != tid) {
-        stamp[r] = tid;
-        added.push_back((int32_t)r);
-      }
-      for (int32_t k = rp[r]; k < rp[r + 1]; ++k) {
-        const int32_t u = ci[k];
-        if (stamp[u] != tid) {
-          stamp[u] = tid;
-          added.push_back(u);
-        }
-      }
+      if (set.insert((int32_t)r)) added.push_back((int32_t)r);
+      for (int32_t k = rp[r]; k < rp[r + 1]; ++k)
+        if (set.insert(ci[k])) added.push_back(ci[k]);
       if ((int64_t)cur.size() + (int64_t)added.size() > ucap) {
-        for (int32_t u : added) stamp[u] = -1;
+        set.erase_last(added.size());
         break;
       }
       cur.insert(cur.end(), added.begin(), added.end());
@@ -168,30 +193,100 @@ bool build_tiles(int64_t n, const int32_t* rp, const int32_t* ci, int ucap, int 
     }
     if (r == t0) return false;  // one row gathers from more than ucap rows
     std::sort(cur.begin(), cur.end());
-    t.ucol.insert(t.ucol.end(), cur.begin(), cur.end());
-    t.uoff.push_back((int64_t)t.ucol.size());
-    t.trow.push_back(r);
-    t.max_union = std::max<int>(t.max_union, (int)cur.size());
-    t.max_rows = std::max<int>(t.max_rows, (int)(r - t0));
-    ++tid;
+    ucol.insert(ucol.end(), cur.begin(), cur.end());
+    ends.push_back((int32_t)r);
+    sizes.push_back((int32_t)cur.size());
   }
   return true;
 }
 
+int host_threads() {
+  const unsigned hc = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(hc, 16u));
+}
+
+}  // namespace
+
+bool build_tiles(int64_t n, const int32_t* rp, const int32_t* ci, int ucap, int tmax,
+                 int nnzcap, TileHost& t) {
+  // row chunks built in parallel (a tile never spans two chunks)
+  const int nt = n > 65536 ? host_threads() : 1;
+  std::vector<std::vector<int32_t>> ends(nt), sizes(nt), ucol(nt);
+  std::vector<char> ok(nt, 1);
+  auto work = [&](int c) {
+    const int64_t lo = n * c / nt, hi = n * (c + 1) / nt;
+    ok[c] = tiles_range(lo, hi, rp, ci, ucap, tmax, nnzcap, ends[c], sizes[c], ucol[c]);
+  };
+  std::vector<std::thread> th;
+  for (int c = 1; c < nt; ++c) th.emplace_back(work, c);
+  work(0);
+  for (auto& x : th) x.join();
+  for (int c = 0; c < nt; ++c)
+    if (!ok[c]) return false;
+  t.trow.assign(1, 0);
+  t.uoff.assign(1, 0);
+  t.ucol.clear();
+  t.max_union = 0;
+  t.max_rows = 0;
+  for (int c = 0; c < nt; ++c) {
+    t.ucol.insert(t.ucol.end(), ucol[c].begin(), ucol[c].end());
+    for (size_t i = 0; i < ends[c].size(); ++i) {
+      t.max_rows = std::max<int>(t.max_rows, ends[c][i] - t.trow.back());
+      t.trow.push_back(ends[c][i]);
+      t.uoff.push_back(t.uoff.back() + sizes[c][i]);
+      t.max_union = std::max<int>(t.max_union, sizes[c][i]);
+    }
+  }
+  return true;
+}
+
+double tile_union_ratio(int64_t n, const int32_t* rp, const int32_t* ci, int ucap, int tmax,
+                        int nnzcap, int windows) {
+  // rows of `windows` evenly spaced windows of n / (8 windows) rows each
+  const int64_t w = std::max<int64_t>(1, n / (8 * (int64_t)windows));
+  std::vector<double> sum(windows, 0.0), rows(windows, 0.0);
+  std::vector<char> ok(windows, 1);
+  auto work = [&](int c) {
+    const int64_t lo = n * c / windows, hi = std::min(n, lo + w);
+    std::vector<int32_t> e, sz, u;
+    ok[c] = tiles_range(lo, hi, rp, ci, ucap, tmax, nnzcap, e, sz, u);
+    sum[c] = (double)u.size();
+    rows[c] = (double)(hi - lo);
+  };
+  std::vector<std::thread> th;
+  for (int c = 1; c < windows; ++c) th.emplace_back(work, c);
+  work(0);
+  for (auto& x : th) x.join();
+  double s = 0.0, r = 0.0;
+  for (int c = 0; c < windows; ++c) {
+    if (!ok[c]) return -1.0;
+    s += sum[c];
+    r += rows[c];
+  }
+  return s / r;
+}
+
 void tile_local_index(int64_t n, const int32_t* rp, const int32_t* ci, const TileHost& t,
                       std::vector<uint16_t>& lidx, std::vector<int32_t>& uself) {
-  std::vector<int32_t> pos(n, -1);
   lidx.assign((size_t)rp[n] + 8, 0);
   const int64_t ntiles = (int64_t)t.trow.size() - 1;
   uself.assign(ntiles, 0);
-  for (int64_t tt = 0; tt < ntiles; ++tt) {
-    const int64_t u0 = t.uoff[tt], u1 = t.uoff[tt + 1];
-    for (int64_t u = u0; u < u1; ++u) pos[t.ucol[u]] = (int32_t)(u - u0);
-    uself[tt] = pos[t.trow[tt]];
-    for (int64_t r = t.trow[tt]; r < t.trow[tt + 1]; ++r)
-      for (int32_t k = rp[r]; k < rp[r + 1]; ++k) lidx[k] = (uint16_t)pos[ci[k]];
-    for (int64_t u = u0; u < u1; ++u) pos[t.ucol[u]] = -1;
-  }
+  const int nt = n > 65536 ? host_threads() : 1;
+  auto work = [&](int c) {
+    // position of a union row within its (sorted) union: binary search
+    for (int64_t tt = ntiles * c / nt; tt < ntiles * (c + 1) / nt; ++tt) {
+      const int32_t* u0 = t.ucol.data() + t.uoff[tt];
+      const int32_t* u1 = t.ucol.data() + t.uoff[tt + 1];
+      uself[tt] = (int32_t)(std::lower_bound(u0, u1, t.trow[tt]) - u0);
+      for (int64_t r = t.trow[tt]; r < t.trow[tt + 1]; ++r)
+        for (int32_t k = rp[r]; k < rp[r + 1]; ++k)
+          lidx[k] = (uint16_t)(std::lower_bound(u0, u1, ci[k]) - u0);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int c = 1; c < nt; ++c) th.emplace_back(work, c);
+  work(0);
+  for (auto& x : th) x.join();
 }
 
 }  // namespace rafeast

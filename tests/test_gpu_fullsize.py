@@ -11,8 +11,9 @@ eigenpairs the library returns:
 * orthonormality of the returned vectors;
 * the eigenspace: sin-theta against the closed-form eigenvectors of the 3-D
   grid; for the kNN graph, which has no reference vectors, the Davis-Kahan
-  bound sin-theta <= ||R||_F / delta (delta: distance of the returned values
-  to the nearest eigenvalue outside the interval, from the stored spectrum)."""
+  bound sin-theta <= ||R||_2 / delta (delta: distance of the returned values
+  to the nearest eigenvalue outside the interval, from the stored spectrum);
+* repeated solves with the tuned kernel shapes return identical bits."""
 import numpy as np
 import pytest
 
@@ -36,8 +37,12 @@ def _checks(a, lam, vec, ref, outside, outer_tol, vec_ref=None):
     assert M.orth_err(vec) <= 1e-10
     if vec_ref is not None:
         return M.sin_theta(vec, vec_ref)
+    # Davis-Kahan sin-theta theorem in the spectral norm: ||sin Theta||_2 <=
+    # ||R||_2 / delta, R = A V - V diag(lam); ||R||_2 from the eigenvalues of
+    # the small Gram matrix R^T R
     delta = min(abs(o - lam).min() for o in outside)
-    return float(np.linalg.norm(r) / delta)
+    r2 = float(np.sqrt(max(np.linalg.eigvalsh(r.T @ r).max(), 0.0)))
+    return r2 / delta
 
 
 @pytest.mark.parametrize("key", ["knn200k", "grid3d"])
@@ -56,8 +61,21 @@ def test_single_problem_full_size(lib, key):
         evecs = np.zeros((cfg.m0, lap.n))
         resid = np.zeros(cfg.m0)
         st, mf, info = lib.rafeast_solve(h, prm, evals, evecs, resid)
+        # two more solves with the shapes the first one tuned: the tiled dot
+        # kernel (kept by the autotuner) adds its sums in a fixed order, so
+        # they repeat to the last bit
+        assert lib.rafeast_profile(h, reset=False)["dots_shape"] >= 1000000
+        again = []
+        for _ in range(2):
+            lib.rafeast_warmstart(h, g["lmin"], g["lmax"], cfg.m0, cfg.p, cfg.q, cfg.seed)
+            e2, v2, r2 = np.zeros(cfg.m0), np.zeros((cfg.m0, lap.n)), np.zeros(cfg.m0)
+            st2, mf2, info2 = lib.rafeast_solve(h, prm, e2, v2, r2)
+            again.append((st2, mf2, info2.outer_iters, e2, v2, r2))
     finally:
         lib.rafeast_destroy(h)
+    (sa, ma, ia, ea, va, ra), (sb, mb, ib, eb, vb, rb) = again
+    assert (sa, ma, ia) == (sb, mb, ib)
+    assert np.array_equal(ea, eb) and np.array_equal(ra, rb) and np.array_equal(va, vb)
     assert st == lib.RAFEAST_OK, info.as_dict()
     assert mf == g["count"]
     lam, vec = evals[:mf], evecs[:mf].T
@@ -66,10 +84,11 @@ def test_single_problem_full_size(lib, key):
         ref_vals, vec_ref = E.grid_eigvecs_in((100, 100, 100), 1e-2, g["lmin"], g["lmax"])
         assert len(ref_vals) == g["count"]
     err = _checks(lap.scipy(), lam, vec, g["evals"], g["neighbours"][:1], cfg.outer_tol, vec_ref)
-    # mixed-path gate on the eigenspace (sin-theta <= 1e-6) where reference
-    # vectors exist; the Davis-Kahan bound is a guaranteed upper bound, which
-    # the stopping tolerance alone keeps below 1e-5 on the kNN graph
-    assert err <= (1e-6 if vec_ref is not None else 1e-5), err
+    # mixed-path gate on the eigenspace: sin-theta <= 1e-6, against the
+    # closed-form eigenvectors of the grid, and for the kNN graph through the
+    # Davis-Kahan bound, a guaranteed upper bound on the distance to the true
+    # eigenspace
+    assert err <= 1e-6, err
 
 
 def test_batched_sbm_full_size(lib):
