@@ -128,6 +128,12 @@ extern "C" {
 #define RAFEAST_OPT_TILE_CB 15      /* with RAFEAST_OPT_TILED = 2: column     *
                                      * pairs per block of the tiled dot kernel *
                                      * (4 or 8; 0 = autotuned)                 */
+#define RAFEAST_OPT_DENSE 16        /* FP64 Gram matrices (Cholesky-QR,       *
+                                     * Rayleigh-Ritz, rafeast_gram): 0 (default)*
+                                     * on the tensor cores, FP64 values split   *
+                                     * into exact BF16 digits with integer      *
+                                     * accumulation (m <= 128); 1 on the FP64   *
+                                     * pipe                                     */
 #define RAFEAST_OPT_TEST_STALL 9    /* test hook: bytes (multiple of 16) that  *
                                      * every bulk-copy stage waits for and no *
                                      * copy delivers, so the bounded wait     *

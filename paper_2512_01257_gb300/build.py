@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librafeast.so")
 SOURCES = ["kernels_sparse.cu", "kernels_batched.cu", "kernels_tma.cu", "kernels_dense.cu",
-           "kernels_tiled.cu", "api.cu", "noalloc.cu", "hostmath.cpp", "tiling.cpp"]
+           "kernels_tiled.cu", "kernels_tc.cu", "api.cu", "noalloc.cu", "hostmath.cpp", "tiling.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -140,6 +140,20 @@ static DenseWs dense_ws(Handle* h, int m) {
   return d;
 }
 
+// G = X^T Y (m x m) of the handle's tall blocks: on the tensor cores (FP64
+// values split into exact BF16 digits, kernels_tc.cu) unless the FP64 pipe is
+// asked for or m exceeds 128; the float Gram of a preconditioning pass stays
+// on the float pipe. sym: the result is symmetric (X^T X, X^T A X) and is
+// made exactly so.
+static void gram_dev(Handle* h, const double* X, const double* Y, int m, int ld, double* G,
+                     const DenseWs& d, bool sym, bool f32 = false) {
+  // (two launches either way; the callers count them)
+  if (!f32 && h->opt_dense == 0 && gram_tc_fits(m))
+    gram_tc(X, Y, h->n, m, ld, G, d.part, h->num_sms, d.status + 3, h->stream, sym);
+  else
+    gram(X, Y, h->n, m, ld, G, d.part, h->num_sms, h->stream, sym, f32);
+}
+
 // X (n x m, ld) <- X R^{-1}; returns number of shifted passes; R_total (host,
 // m x m row-major upper) accumulates the factor if non-null. low_first: the
 // first pass forms its Gram in float, as in cholqr_rr below (the pass only
@@ -160,7 +174,7 @@ static int cholqr(Handle* h, double*& X, double*& tmp, int m, int ld, std::vecto
     int st = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
       const bool f32 = low && attempt == 0;
-      gram(X, X, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true, f32);
+      gram_dev(h, X, X, m, ld, d.G, d, true, f32);
       chol_inv(d.G, m, h->n, d.R, d.Rinv, d.status, h->stream, low_used && pass == 1);
       h->launches += 3;
       RF_CUDA(cudaMemcpyAsync(&st, d.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -207,7 +221,7 @@ static void rayleigh_ritz_dev(Handle* h, const double* X, int m, int ld, double*
   DenseWs d = dense_ws(h, m);
   launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m, ld, 1.0, h->shift, X, tmp,
                            h->num_sms, h->stream);
-  gram(X, tmp, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true);
+  gram_dev(h, X, tmp, m, ld, d.G, d, true);
   jacobi_eigh(d.G, m, theta_d, d.V, d.Vw, h->stream);
   tall_gemm(X, h->n, m, ld, d.V, m, Qout, ld, h->stream);
   // A Q by the (memory-bound) SpMM rather than (A X) V by an FP64 GEMM
@@ -241,7 +255,7 @@ static int cholqr_rr(Handle* h, double*& X, double*& tmp, double* tmp2, int m, i
     int st = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
       const bool f32 = low && attempt == 0;
-      gram(X, X, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true, f32);
+      gram_dev(h, X, X, m, ld, d.G, d, true, f32);
       chol_inv(d.G, m, h->n, d.R, d.Rinv, d.status, h->stream, low_used && pass == 1);
       h->launches += 3;
       RF_CUDA(cudaMemcpyAsync(&st, d.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -268,7 +282,7 @@ static int cholqr_rr(Handle* h, double*& X, double*& tmp, double* tmp2, int m, i
   RF_CUDA(cudaEventRecord(ev_mid, h->stream));
   launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m, ld, 1.0, h->shift, X, tmp2,
                            h->num_sms, h->stream);
-  gram(X, tmp2, h->n, m, ld, d.G, d.part, h->num_sms, h->stream, true);  // X^T A X
+  gram_dev(h, X, tmp2, m, ld, d.G, d, true);  // X^T A X
   small_gemm(d.G, 0, d.Rinv, 0, d.R, m, 1.0, 0.0, h->stream);            // (X^T A X) R^-1
   small_gemm(d.Rinv, 1, d.R, 0, d.G, m, 1.0, 0.0, h->stream);            // R^-T (.)
   jacobi_eigh(d.G, m, theta_d, d.V, d.Vw, h->stream);
@@ -1872,6 +1886,10 @@ int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
       if (value < 0 || value > 2) return RAFEAST_ERR_INVALID_ARG;
       h->opt_tiled = (int)value;
       return RAFEAST_OK;
+    case RAFEAST_OPT_DENSE:
+      if (value < 0 || value > 1) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_dense = (int)value;
+      return RAFEAST_OK;
     case RAFEAST_OPT_TILE_CB:
       if (value != 0 && value != 4 && value != 8) return RAFEAST_ERR_INVALID_ARG;
       h->opt_tile_cb = (int)value;
@@ -2158,12 +2176,15 @@ int rafeast_gram(rafeast_t hh, int m, const double* X, const double* Y, double* 
   CallScope scope(h);
   const int ld = even(m);
   double* Xi = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ld);
-  double* Yi = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ld);
+  double* Yi = Xi;
   launch_to_internal(h->n, m, X, Xi, ld, h->perm, h->stream);
-  launch_to_internal(h->n, m, Y, Yi, ld, h->perm, h->stream);
+  if (Y != X) {  // (the same block twice: X^T X, one copy and one digit split)
+    Yi = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ld);
+    launch_to_internal(h->n, m, Y, Yi, ld, h->perm, h->stream);
+  }
   DenseWs d = dense_ws(h, m);
   // row-major (Y^T X)[b][a] = sum_r Y[r][b] X[r][a] is G = X^T Y in column-major order
-  gram(Yi, Xi, h->n, m, ld, G, d.part, h->num_sms, h->stream);
+  gram_dev(h, Yi, Xi, m, ld, G, d, X == Y);
   h->launches += 4;
   scope.finish();
   RF_CUDA(cudaStreamSynchronize(h->stream));
@@ -2243,7 +2264,7 @@ int rafeast_warmstart(rafeast_t hh, double lmin, double lmax, int m0, int p, int
     DenseWs d = dense_ws(h, k);
     launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, k, ld, 1.0, h->shift, Y, AY,
                              h->num_sms, h->stream);
-    gram(Y, AY, h->n, k, ld, d.G, d.part, h->num_sms, h->stream, true);
+    gram_dev(h, Y, AY, k, ld, d.G, d, true);
     jacobi_eigh(d.G, k, th_all, d.V, d.Vw, h->stream);
     h->launches += 4;
     h->spmm_launches += 1;

@@ -237,6 +237,7 @@ struct Handle {
   int opt_values_free = 0;  // 0: values-free gathers for unit Laplacians, 1: never
   int opt_tiled = 0;        // seed dot kernel: 0 auto (tiled when built), 1 never, 2 only tiled
   int opt_tile_cb = 0;      // tiled dot kernel: forced column pairs per block (0: autotuned)
+  int opt_dense = 0;        // FP64 Gram matrices: 0 tensor cores (digit split), 1 FP64 pipe
   // autotuned kernel shapes (lanes, chunks per lane) of the multi-shift
   // kernels, keyed by (pairs, shifts, precision)
   struct Shape {
@@ -404,6 +405,15 @@ void launch_from_internal(int64_t n, int m, const double* src, int ld, double* d
 // mixed-precision Cholesky-QR
 void gram(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
           double* partial, int num_sms, cudaStream_t s, bool sym = false, bool f32 = false);
+// G = sum of the m x m partials in increasing order (sym: the 16-blocks below
+// the diagonal taken from above it, so G is exactly symmetric)
+void gram_sum(const double* part, int parts, int m, bool sym, double* G, cudaStream_t s);
+// the same Gram on the tensor cores (kernels_tc.cu): FP64 values split into
+// exact BF16 digits, tcgen05 products, exact integer accumulation; m <= 128,
+// partial: num_sms * m * m doubles; err (may be null) set on a timed-out wait
+bool gram_tc_fits(int m);
+void gram_tc(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
+             double* partial, int num_sms, int* err, cudaStream_t s, bool sym);
 // Y = X * M (M: m x mo, ld mo); upper: M is upper triangular (m == mo)
 void tall_gemm(const double* X, int64_t n, int m, int ldx, const double* M, int mo,
                double* Y, int ldy, cudaStream_t s, bool upper = false);

@@ -244,20 +244,34 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
     }
 }
 
-// sym: entries (a, b) with a / 16 > b / 16 were not computed; take (b, a)
+// sym: entries (a, b) with a / 16 > b / 16 were not computed; take (b, a).
+// The partials are added in increasing order with Neumaier's compensated
+// summation (A. Neumaier, ZAMM 54, 1974): the rounding error of every
+// addition is carried along, so the sum of the CTAs' partials adds about
+// two units of rounding instead of one per partial.
 __global__ void k_gram_sum(const double* __restrict__ part, int nparts, int m, int sym,
                            double* G) {
   const int mm = m * m;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += gridDim.x * blockDim.x) {
     const int a = e / m, b = e - a * m;
     const int src = (sym && (a >> 4) > (b >> 4)) ? b * m + a : e;
-    double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * mm + src];
-    G[e] = s;
+    double s = 0.0, c = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+      const double v = part[(int64_t)p * mm + src];
+      const double t = s + v;
+      c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+      s = t;
+    }
+    G[e] = s + c;
   }
 }
 
 int gram_parts(int num_sms) { return 2 * num_sms; }
+
+void gram_sum(const double* part, int parts, int m, bool sym, double* G, cudaStream_t s) {
+  k_gram_sum<<<(m * m + 255) / 256, 256, 0, s>>>(part, parts, m, sym ? 1 : 0, G);
+  RF_LAUNCH();
+}
 
 template <bool SYM, typename A = double>
 static void gram_partials(const double* X, const double* Y, int64_t n, int m, int ld,

@@ -1,0 +1,417 @@
+// FP64 Gram matrices G = X^T Y on the tensor cores (tcgen05, sm_103a), by
+// splitting FP64 values into exact BF16 digits (the error-free splitting of
+// Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012).
+//
+// The Gram matrices of the Cholesky-QR and Rayleigh-Ritz steps (Algorithm 1)
+// are n x m by n x m contractions with n up to 10^6 and m <= 128. On this part
+// the FP64 pipe issues 2 operations per SM per clock; the BF16 tensor cores do
+// several thousand. So:
+//
+// 1. Scaling. A CTA owns a range of rows. For every column of X (and of Y)
+//    it takes the largest binary exponent over its rows, E, so that every
+//    value of the column is below 2^E in magnitude, and writes each value as
+//    the integer F = round(x 2^(55-E)), |F| <= 2^55 (the value to 2^-55
+//    relative to the column's largest; integer operations only).
+// 2. Digits. F = sum_{i=0..6} d_i 2^(8 (6-i)) with balanced digits
+//    d_i in [-128, 128] (a carry moves every digit of 128 or more up), each
+//    exact in BF16.
+// 3. Products. x_a y_b = 2^(Ea+Eb-14) sum_{i,j} d_i d_j 2^(-8 (i+j)). The
+//    pairs with i + j = l form level l; levels 0..6 are kept (the next would
+//    change the result by 2^-56 of sum_k |x_ka y_kb|). A level is one TMEM
+//    accumulator of FP32: its 28 pairs are 28 tcgen05.mma (M = 128 rows a,
+//    N <= 64 columns b, K = 16 rows k) per 16 rows of X.
+// 4. Exactness. A product of two digits is an integer of at most 2^14 and
+//    level l adds l + 1 of them per row, so over 128 rows levels 0..3 stay
+//    integers of magnitude <= 2^23 and FP32 holds them exactly. Every 128
+//    rows those four levels are read out of TMEM and added, as one integer
+//    sum_{l<=3} S_l 2^(8 (3-l)), into a 64-bit integer per entry; the next
+//    MMAs restart them. Levels 4..6 keep accumulating in FP32 over the CTA's
+//    rows: their rounding is below 2^-24 of terms that are themselves below
+//    2^-32 of the result.
+// 5. The CTA's partial Gram is (I + L 2^-8) 2^(Ea+Eb-38), I the integer and
+//    L = S_4 + S_5 2^-8 + S_6 2^-16; the partials of all CTAs are added in a
+//    fixed order (k_gram_sum), so the result does not depend on scheduling.
+//
+// Operands are staged in shared memory in the canonical K-major layout
+// without swizzle (core matrices of 8 rows x 16 bytes; the descriptor's
+// leading offset is the step between the two 8-element halves of a 16-wide
+// K slice, its stride offset the step between 8-row groups), two buffers of
+// 32 rows each: the digits of the next 32 rows are formed while the tensor
+// cores multiply the last ones. One thread issues the MMAs and commits them
+// to an mbarrier per buffer; every wait on it is bounded.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace rafeast {
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int TC_M = 128;               // MMA rows: Gram rows a (m <= 128)
+constexpr int TC_KS = 32;               // rows of X per sub-chunk (two K = 16 steps)
+constexpr int TC_SUB_PER_CHUNK = 4;     // sub-chunks per exact chunk (128 rows)
+constexpr int TC_NB = 64;               // most Gram columns b per CTA
+constexpr int TC_LEV = 7;               // levels kept (digit pairs with i + j <= 6)
+constexpr int TC_DIG = 7;               // digits per value
+constexpr uint32_t TC_LBO = 128;        // byte step between the two K halves of a K = 16 slice
+constexpr uint32_t TC_SBO = 512;        // byte step between 8-row groups (32 rows of K = 4 cores)
+constexpr int TC_APLANE = TC_M * TC_KS * 2;   // bytes of one digit plane of X^T (8 KB)
+constexpr int TC_BPLANE = TC_NB * TC_KS * 2;  // bytes of one digit plane of Y^T (4 KB)
+constexpr long long TC_WAIT = 200000000;      // bounded mbarrier polls (~ seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of (row r, k) in a K-major plane of 32 K columns
+__device__ __forceinline__ uint32_t tc_off(int r, int k) {
+  return (uint32_t)((r & 7) * 16 + (k & 7) * 2 + (k >> 3) * 128 + (r >> 3) * TC_SBO);
+}
+
+// shared-memory matrix descriptor: start, leading and stride byte offsets,
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((TC_SBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = n columns, M = 128
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(mbar))
+      : "memory");
+}
+
+// bounded wait for phase `parity` of an mbarrier; false when it ran out
+__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long long it = 0; it < TC_WAIT && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+
+// 8 FP32 columns of TMEM for this warp's 32 lanes
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+#pragma unroll
+  for (int t = 0; t < 8; ++t) v[t] = __uint_as_float(r[t]);
+}
+__device__ __forceinline__ void tc_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// F = round(x 2^(55 - E)), E = ebias - 1022 for ebias the largest biased
+// exponent of the column (|x| < 2^E); integer operations only
+__device__ __forceinline__ long long tc_fixed(double x, int ebias) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return 0;  // zero, or below 2^-1022
+  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  const int sh = e - ebias + 2;  // x = mant 2^(e-1075): F = mant 2^(e - 1075 + 55 - E)
+  long long F;
+  if (sh >= 0) F = mant << sh;  // sh <= 2: F < 2^55
+  else if (sh > -54) F = (mant + (1ll << (-sh - 1))) >> (-sh);
+  else F = 0;
+  return (b >> 63) ? -F : F;
+}
+
+// balanced base-256 digits, d[0] most significant
+__device__ __forceinline__ void tc_digits(long long F, int (&d)[TC_DIG]) {
+#pragma unroll
+  for (int i = TC_DIG - 1; i > 0; --i) {
+    int v = (int)(F & 255);
+    F >>= 8;
+    if (v >= 128) {
+      v -= 256;
+      F += 1;
+    }
+    d[i] = v;
+  }
+  d[0] = (int)F;
+}
+
+// two values at consecutive k of one row into the 7 digit planes (one 32-bit
+// store per plane)
+__device__ __forceinline__ void tc_store_pair(unsigned char* planes, int plane_bytes,
+                                              uint32_t off, long long F0, long long F1) {
+  int d0[TC_DIG], d1[TC_DIG];
+  tc_digits(F0, d0);
+  tc_digits(F1, d1);
+#pragma unroll
+  for (int i = 0; i < TC_DIG; ++i) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn((float)d0[i], (float)d1[i]);
+    *reinterpret_cast<__nv_bfloat162*>(planes + i * plane_bytes + off) = p;
+  }
+}
+
+// G partial of one CTA: rows [k_lo, k_hi) of X and Y, Gram rows a < m (all),
+// Gram columns b0 .. b0 + nb (nb a multiple of 16, <= 64). SYM: Y == X, the
+// B operand is read from X's digit planes.
+template <bool SYM>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_gram(const double* __restrict__ X, const double* __restrict__ Y, int64_t n, int m,
+              int ld, int nb, double* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  constexpr int BUF = TC_DIG * TC_APLANE + (SYM ? 0 : TC_DIG * TC_BPLANE);
+  __shared__ int sEa[TC_M], sEb[TC_NB];
+  __shared__ uint32_t s_tbase;
+  __shared__ __align__(8) uint64_t s_mbar[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b0 = blockIdx.y * nb;
+  const int64_t k_lo = n * (int64_t)blockIdx.x / gridDim.x;
+  const int64_t k_hi = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  // column exponents over this CTA's rows
+  for (int t = tid; t < TC_M; t += TC_THREADS) sEa[t] = 0;
+  for (int t = tid; t < TC_NB; t += TC_THREADS) sEb[t] = 0;
+  __syncthreads();
+  {
+    const int a = tid & (TC_M - 1);
+    int e = 0;
+    if (a < m)
+      for (int64_t r = k_lo + (tid >> 7); r < k_hi; r += 2)
+        e = max(e, (int)(((unsigned long long)__double_as_longlong(X[r * ld + a]) >> 52) & 0x7FF));
+    atomicMax(&sEa[a], e);
+    if (!SYM) {
+      const int b = tid & (TC_NB - 1);
+      int f = 0;
+      if (b < nb && b0 + b < m)
+        for (int64_t r = k_lo + (tid >> 6); r < k_hi; r += 4)
+          f = max(f, (int)(((unsigned long long)__double_as_longlong(Y[r * ld + b0 + b]) >> 52) &
+                           0x7FF));
+      atomicMax(&sEb[b], f);
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tbase)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = s_tbase;
+  const uint32_t idesc = tc_idesc(nb);
+  // readout mapping: lane row a, half h of the nb columns
+  const int ra = 32 * (warp & 3) + lane;
+  const int h = warp >> 2, nh = nb >> 1;
+  const uint32_t trow = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+  long long acc[TC_NB / 2];
+#pragma unroll
+  for (int c = 0; c < TC_NB / 2; ++c) acc[c] = 0;
+  bool ok = true;
+  // levels 0..3 of the finished chunk into the integer sums
+  auto read_exact = [&]() {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+#pragma unroll
+      for (int c8 = 0; c8 < TC_NB / 2; c8 += 8) {
+        if (c8 < nh) {
+          float v[8];
+          tc_ld8(trow + l * nb + h * nh + c8, v);
+          tc_ld_wait();
+#pragma unroll
+          for (int t = 0; t < 8; ++t) acc[c8 + t] += __float2ll_rn(v[t]) * (1ll << (8 * (3 - l)));
+        }
+      }
+    }
+  };
+  const int64_t rows = k_hi - k_lo;
+  const int nsub = (int)((rows + TC_KS - 1) / TC_KS);
+  for (int s = 0; s < nsub && ok; ++s) {
+    const int buf = s & 1;
+    unsigned char* A = tsm + buf * BUF;
+    unsigned char* B = A + TC_DIG * TC_APLANE;
+    // (every wait's outcome is made CTA-uniform before anyone acts on it)
+    if (s >= 2) ok = __syncthreads_and(tc_wait(&s_mbar[buf], ((s - 2) >> 1) & 1));
+    if (!ok) break;
+    // digits of rows k_lo + 32 s .. + 32 (zero past k_hi and for a >= m);
+    // every load of the sub-chunk is issued before any digit is formed
+    const int64_t rbase = k_lo + (int64_t)s * TC_KS;
+    {
+      const int a = tid & (TC_M - 1);
+      const int eb = sEa[a];
+      double xv[TC_KS / 2];
+#pragma unroll
+      for (int q = 0; q < TC_KS / 4; ++q) {
+        const int kp = (tid >> 7) + 2 * q;
+        const int64_t r = rbase + 2 * kp;
+        xv[2 * q] = (a < m && r < k_hi) ? X[r * ld + a] : 0.0;
+        xv[2 * q + 1] = (a < m && r + 1 < k_hi) ? X[(r + 1) * ld + a] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < TC_KS / 4; ++q) {
+        const int kp = (tid >> 7) + 2 * q;
+        tc_store_pair(A, TC_APLANE, tc_off(a, 2 * kp), tc_fixed(xv[2 * q], eb),
+                      tc_fixed(xv[2 * q + 1], eb));
+      }
+    }
+    if (!SYM) {
+      const int b = tid & (TC_NB - 1);
+      const int eb = sEb[b];
+      const bool on = b < nb && b0 + b < m;
+      double yv[TC_KS / 4];
+#pragma unroll
+      for (int q = 0; q < TC_KS / 8; ++q) {
+        const int kp = (tid >> 6) + 4 * q;
+        const int64_t r = rbase + 2 * kp;
+        yv[2 * q] = (on && r < k_hi) ? Y[r * ld + b0 + b] : 0.0;
+        yv[2 * q + 1] = (on && r + 1 < k_hi) ? Y[(r + 1) * ld + b0 + b] : 0.0;
+      }
+      if (b < nb) {
+#pragma unroll
+        for (int q = 0; q < TC_KS / 8; ++q) {
+          const int kp = (tid >> 6) + 4 * q;
+          tc_store_pair(B, TC_BPLANE, tc_off(b, 2 * kp), tc_fixed(yv[2 * q], eb),
+                        tc_fixed(yv[2 * q + 1], eb));
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    const bool chunk_start = (s % TC_SUB_PER_CHUNK) == 0;
+    if (s > 0 && chunk_start) {
+      // the previous chunk is complete once the last sub-chunk's MMAs are
+      ok = __syncthreads_and(tc_wait(&s_mbar[(s - 1) & 1], ((s - 1) >> 1) & 1));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (ok) read_exact();
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (!ok) break;
+    }
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_base = smem_u32(A);
+      const uint32_t b_base = SYM ? a_base + (uint32_t)(b0 >> 3) * TC_SBO : smem_u32(B);
+      const int bplane = SYM ? TC_APLANE : TC_BPLANE;
+      // descriptors differ only in their start address (16-byte units in the
+      // low bits): one base per operand, plane and K-step offsets added
+      const uint64_t ad0 = tc_desc(a_base), bd0 = tc_desc(b_base);
+#pragma unroll
+      for (int ks = 0; ks < TC_KS / 16; ++ks) {
+#pragma unroll
+        for (int l = 0; l < TC_LEV; ++l) {
+          const bool fresh = ks == 0 && (l <= 3 ? chunk_start : s == 0);
+#pragma unroll
+          for (int i = 0; i <= l; ++i) {
+            const int j = l - i;
+            const uint64_t ad = ad0 + (uint64_t)((i * TC_APLANE + ks * 256) >> 4);
+            const uint64_t bd = bd0 + (uint64_t)((j * bplane + ks * 256) >> 4);
+            tc_mma(tbase + l * nb, ad, bd, idesc, (fresh && i == 0) ? 0u : 1u);
+          }
+        }
+      }
+      tc_commit(&s_mbar[buf]);
+    }
+  }
+  // the last chunk: levels 0..3 into the integers, levels 4..6 as the
+  // correction; the CTA's partial Gram scaled back
+  if (ok && nsub > 0) ok = tc_wait(&s_mbar[(nsub - 1) & 1], ((nsub - 1) >> 1) & 1);
+  ok = __syncthreads_and(ok);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok && nsub > 0) read_exact();
+  const int a = ra;
+  double* out = part + (int64_t)blockIdx.x * m * m;
+#pragma unroll
+  for (int c8 = 0; c8 < TC_NB / 2; c8 += 8) {
+    if (c8 < nh) {
+      float s4[8], s5[8], s6[8];
+      if (ok && nsub > 0) {
+        tc_ld8(trow + 4 * nb + h * nh + c8, s4);
+        tc_ld8(trow + 5 * nb + h * nh + c8, s5);
+        tc_ld8(trow + 6 * nb + h * nh + c8, s6);
+        tc_ld_wait();
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int b = b0 + h * nh + c8 + t;
+        if (a < m && b < m) {
+          double v = ok ? 0.0 : __longlong_as_double(0x7ff8000000000000ll);  // NaN on a timeout
+          if (ok && nsub > 0) {
+            const float lo = fmaf(s6[t], 0x1p-16f, fmaf(s5[t], 0x1p-8f, s4[t]));
+            const int ea = sEa[a], ebb = SYM ? sEa[b] : sEb[h * nh + c8 + t];
+            // (I + L 2^-8) 2^(Ea + Eb - 38), Ea = ea - 1022, Eb = eb - 1022
+            const int p = ea + ebb - 2044 - 38;
+            // two normal powers of two (results below 2^-2044 flush to zero)
+            const int p1 = max(-1022, min(1023, p / 2)), p2 = max(-1022, min(1023, p - p / 2));
+            v = fma((double)lo, 0x1p-8, (double)acc[c8 + t]);
+            v = v * __longlong_as_double((long long)(p1 + 1023) << 52) *
+                __longlong_as_double((long long)(p2 + 1023) << 52);
+            if (ea == 0 || ebb == 0) v = 0.0;
+          }
+          out[(int64_t)a * m + b] = v;
+        }
+      }
+    }
+  }
+  if (!ok && tid == 0 && err) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+}
+
+}  // namespace
+
+bool gram_tc_fits(int m) { return m >= 1 && m <= TC_M; }
+
+int gram_tc_parts(int num_sms) { return num_sms; }
+
+void gram_tc(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
+             double* partial, int num_sms, int* err, cudaStream_t s, bool sym) {
+  // X == Y: the B operand is read from X's digits (one split per value)
+  const bool same = X == Y;
+  RF_CHECK(gram_tc_fits(m), RAFEAST_ERR_INVALID_ARG);
+  const int nblk = (m + TC_NB - 1) / TC_NB;
+  int nb = (m + nblk - 1) / nblk;
+  nb = ((nb + 15) / 16) * 16;
+  const int nby = (m + nb - 1) / nb;
+  const int parts = gram_tc_parts(num_sms);
+  dim3 grid(parts, nby);
+  if (same) {
+    const size_t smem = 2 * (size_t)TC_DIG * TC_APLANE;
+    ensure_dyn_smem(reinterpret_cast<const void*>(k_tc_gram<true>), smem);
+    k_tc_gram<true><<<grid, TC_THREADS, smem, s>>>(X, X, n, m, ld, nb, partial, err);
+  } else {
+    const size_t smem = 2 * ((size_t)TC_DIG * TC_APLANE + (size_t)TC_DIG * TC_BPLANE);
+    ensure_dyn_smem(reinterpret_cast<const void*>(k_tc_gram<false>), smem);
+    k_tc_gram<false><<<grid, TC_THREADS, smem, s>>>(X, Y, n, m, ld, nb, partial, err);
+  }
+  RF_LAUNCH();
+  gram_sum(partial, parts, m, sym, G, s);
+}
+
+}  // namespace rafeast
