@@ -145,7 +145,10 @@ typedef struct rafeast_ctx* rafeast_t;
 typedef struct rafeast_params {
   double lmin, lmax;     /* search interval, lmin < lmax                      */
   int32_t m0;            /* subspace size, 1..128, > eigenvalues inside       */
-  int32_t nc;            /* quadrature nodes on the half contour, 1..8         */
+  int32_t nc;            /* quadrature nodes on the half contour, 1..16; one  *
+                          * COCG per shift (RAFEAST_OPT_SOLVER = 0) runs up   *
+                          * to 8, more run multi-shift with the streamed      *
+                          * update                                            */
   double ellipse_ratio;  /* imaginary/real semi-axis ratio e, (0, 1]           */
   double solve_tol;      /* COCG: stop when ||r||_2 <= solve_tol * ||b||_2     */
   double outer_tol;      /* stop when max in-interval ||Av-lv||/||A||_1 <= tol */

@@ -741,7 +741,8 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
                           const std::vector<double>& theta, int m0, int ldq, double* Qt,
                           FilterStats& fs) {
   const bool fp64 = sizeof(T) == 8;
-  const bool stream = h->opt_update != 1;
+  // (the gathering update is compiled for up to 8 shifts)
+  const bool stream = h->opt_update != 1 || prm.nc > 8;
   MsProblem<T> P = ms_setup<T>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, nullptr,
                                 h->opt_profile != 0, stream, h->stream);
   const CocgArgs<T>& a = P.a;
@@ -1039,7 +1040,8 @@ static void filter_ms_batched(std::vector<BatchItem*>& items, Handle* owner, cud
   for (int t = 0; t < cnt; ++t) {
     Handle* h = items[t]->h;
     P[t] = ms_setup<T>(h, *items[t]->prm, h->Q, h->AQ, h->theta_d, h->theta, h->m0, h->ldq,
-                       ctl_d + t, owner->opt_profile != 0, owner->opt_update != 1, bs);
+                       ctl_d + t, owner->opt_profile != 0,
+                       owner->opt_update != 1 || items[t]->prm->nc > 8, bs);
   }
   GroupDev<T> gd;
   gd.args_d = (const CocgArgs<T>*)(bb + o_ad);
@@ -1262,7 +1264,7 @@ static void validate_params(const rafeast_params* p) {
   RF_CHECK(std::isfinite(p->lmin) && std::isfinite(p->lmax) && p->lmin < p->lmax,
            RAFEAST_ERR_INVALID_ARG);
   RF_CHECK(p->m0 >= 1 && p->m0 <= 128, RAFEAST_ERR_INVALID_ARG);
-  RF_CHECK(p->nc >= 1 && p->nc <= 8, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(p->nc >= 1 && p->nc <= 16, RAFEAST_ERR_INVALID_ARG);
   RF_CHECK(p->ellipse_ratio > 0.0 && p->ellipse_ratio <= 1.0, RAFEAST_ERR_INVALID_ARG);
   RF_CHECK(p->solve_tol >= 0.0 && p->outer_tol >= 0.0, RAFEAST_ERR_INVALID_ARG);
   RF_CHECK(p->max_outer >= 1 && p->max_inner >= 1, RAFEAST_ERR_INVALID_ARG);
@@ -1276,7 +1278,8 @@ static void validate_params(const rafeast_params* p) {
 static void run_filter(Handle* h, const rafeast_params& prm, const double* Qd, const double* AQd,
                        const double* theta_d, const std::vector<double>& theta, int m0, int ldq,
                        double* Qt, FilterStats& fs) {
-  const bool ms = h->opt_solver == 1 && h->opt_kernel != 2;
+  // one COCG per shift is compiled for up to 8 shifts: more go multi-shift
+  const bool ms = (h->opt_solver == 1 && h->opt_kernel != 2) || prm.nc > 8;
   if (prm.precision == RAFEAST_FP64) {
     if (ms) filter_ms_dev<double>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, Qt, fs);
     else filter_dev<double>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, Qt, fs);

@@ -455,15 +455,17 @@ __host__ __device__ inline size_t ms_stream_smem(int pairs, int ns) {
 }
 
 // the problem's coefficients and column activity into shared memory
+// (NS < 0: the shift count a.ns is read at run time)
 template <typename T, int NS>
 __device__ __forceinline__ void ms_stream_stage(const CocgArgs<T>& a, unsigned char* smem) {
   const int P = a.m0;
+  const int ns = NS < 0 ? a.ns : NS;
   Coef<T>* scf = reinterpret_cast<Coef<T>*>(smem);
   ShiftCoef<T>* ssc = reinterpret_cast<ShiftCoef<T>*>(smem + sizeof(Coef<T>) * 2 * P);
-  int* sact = reinterpret_cast<int*>(smem + (sizeof(Coef<T>) + NS * sizeof(ShiftCoef<T>)) * 2 * P);
+  int* sact = reinterpret_cast<int*>(smem + (sizeof(Coef<T>) + ns * sizeof(ShiftCoef<T>)) * 2 * P);
   for (int t = threadIdx.x; t < 2 * P; t += blockDim.x) scf[t] = a.cf[t];
-  if (NS > 0)
-    for (int t = threadIdx.x; t < 2 * P * NS; t += blockDim.x) ssc[t] = a.scf[t];
+  if (ns > 0)
+    for (int t = threadIdx.x; t < 2 * P * ns; t += blockDim.x) ssc[t] = a.scf[t];
   for (int t = threadIdx.x; t < P; t += blockDim.x) sact[t] = __ldcg(a.colact + t);
   __syncthreads();
 }
@@ -480,11 +482,12 @@ __device__ __forceinline__ void ms_stream_elems(const CocgArgs<T>& a, const unsi
                                                 int64_t lo, bool down) {
   using C = c2<T>;
   const int P = a.m0;
+  const int ns = NS < 0 ? a.ns : NS;
   const Coef<T>* scf = reinterpret_cast<const Coef<T>*>(smem);
   const ShiftCoef<T>* ssc =
       reinterpret_cast<const ShiftCoef<T>*>(smem + sizeof(Coef<T>) * 2 * P);
   const int* sact = reinterpret_cast<const int*>(
-      smem + (sizeof(Coef<T>) + NS * sizeof(ShiftCoef<T>)) * 2 * P);
+      smem + (sizeof(Coef<T>) + ns * sizeof(ShiftCoef<T>)) * 2 * P);
   T* __restrict__ R = a.r[0];
   T* __restrict__ Pd = a.p[0];
   const T* __restrict__ W = a.wbuf;
@@ -512,11 +515,11 @@ __device__ __forceinline__ void ms_stream_elems(const CocgArgs<T>& a, const unsi
       dsum[h] = fma(cf.ca.x, pn.x, fma(-cf.ca.y, pn.y, dsum[h]));
     }
 #pragma unroll
-    for (int t = 0; t < NS; ++t) {
-      const ShiftCoef<T> s0 = ssc[(2 * q) * NS + t];
-      const ShiftCoef<T> s1 = ssc[(2 * q + 1) * NS + t];
+    for (int t = 0; t < (NS < 0 ? ns : NS); ++t) {
+      const ShiftCoef<T> s0 = ssc[(2 * q) * ns + t];
+      const ShiftCoef<T> s1 = ssc[(2 * q + 1) * ns + t];
       if (s0.act != (T)0 || s1.act != (T)0) {
-        T* pp = a.ps + (row * a.ldps + 2 * ((int64_t)q * NS + t)) * 2;
+        T* pp = a.ps + (row * a.ldps + 2 * ((int64_t)q * ns + t)) * 2;
         C pj[2];
         ldcg_chunk<2>(pp, pj);
 #pragma unroll

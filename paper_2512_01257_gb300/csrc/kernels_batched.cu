@@ -299,7 +299,9 @@ static const void* stream_fn(int ns) {
     case 5: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 5>);
     case 6: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 6>);
     case 7: return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, 7>);
-    default: throw Err{RAFEAST_ERR_INVALID_ARG};
+    default:  // N_c = 9..16: the shift count read at run time
+      if (ns < 0 || ns > 15) throw Err{RAFEAST_ERR_INVALID_ARG};
+      return reinterpret_cast<const void*>(k_ms_update_stream_grouped<T, -1>);
   }
 }
 

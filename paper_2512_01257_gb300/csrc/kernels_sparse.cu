@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(THREADS) k_ms_update_stream(CocgArgs<T> a) {
 
 template <typename T, int NS>
 static void dispatch_ms_update_stream(const CocgArgs<T>& a, int num_sms, cudaStream_t s) {
-  const size_t smem = ms_stream_smem<T>(a.m0, NS);
+  // (NS < 0: the instance reads the shift count a.ns at run time)
+  const size_t smem = ms_stream_smem<T>(a.m0, NS < 0 ? a.ns : NS);
   auto kern = k_ms_update_stream<T, NS>;
   if (smem > 48 * 1024) ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
   int occ = 0;
@@ -332,7 +333,10 @@ void launch_ms_update_stream(const CocgArgs<T>& a, int num_sms, cudaStream_t s) 
     case 5: dispatch_ms_update_stream<T, 5>(a, num_sms, s); break;
     case 6: dispatch_ms_update_stream<T, 6>(a, num_sms, s); break;
     case 7: dispatch_ms_update_stream<T, 7>(a, num_sms, s); break;
-    default: throw Err{RAFEAST_ERR_INVALID_ARG};
+    default:  // N_c = 9..16: the shift count read at run time
+      if (a.ns < 0 || a.ns > 15) throw Err{RAFEAST_ERR_INVALID_ARG};
+      dispatch_ms_update_stream<T, -1>(a, num_sms, s);
+      break;
   }
 }
 template void launch_ms_update_stream<float>(const CocgArgs<float>&, int, cudaStream_t);

@@ -123,8 +123,10 @@ def test_status_codes(lib):
         bad = lib.make_params(1.0, 0.5, 6, 2)
         with pytest.raises(lib.RafeastError):
             _solve(lib, h, bad, lap.n)
-        with pytest.raises(lib.RafeastError):
-            _solve(lib, h, lib.make_params(0.0, 1.0, 6, 9), lap.n)
+        # N_c in 1..16 (one quadrature node per shifted solve)
+        for nc in (0, 17):
+            with pytest.raises(lib.RafeastError):
+                _solve(lib, h, lib.make_params(0.0, 1.0, 6, nc), lap.n)
         # subspace start without a subspace of that size
         prm = lib.make_params(0.0, 0.1, 7, 2, start=lib.RAFEAST_START_SUBSPACE)
         with pytest.raises(lib.RafeastError):

@@ -240,11 +240,13 @@ def _filter_case():
 
 @pytest.mark.parametrize("solver", [0, 1, 2])
 @pytest.mark.parametrize("form", ["direct", "correction"])
-@pytest.mark.parametrize("nc,e", [(1, 1.0), (2, 1.0), (3, 0.5), (4, 1.0), (5, 0.3), (8, 1.0)])
+@pytest.mark.parametrize("nc,e", [(1, 1.0), (2, 1.0), (3, 0.5), (4, 1.0), (5, 0.3), (8, 1.0),
+                                  (12, 1.0), (16, 0.5)])
 def test_filter_fp64(lib, form, nc, e, solver):
     """solver 0: one COCG per shift; 1, 2: multi-shift COCG (one seed
     recurrence per column, the other shifts from its scalars) with the
-    gathering and the streamed update kernel."""
+    gathering and the streamed update kernel. N_c above 8 (up to 16) always
+    runs multi-shift with the streamed update and a run-time shift count."""
     import torch
     lap, lmin, lmax = _filter_case()
     m0 = 11
@@ -261,9 +263,12 @@ def test_filter_fp64(lib, form, nc, e, solver):
         got = from_colmajor(Qt)
         assert np.linalg.norm(got - exp) <= 1e-10 * np.linalg.norm(exp)
         # same recurrence up to rounding: at a tolerance near the attainable
-        # accuracy the step counts of the two CG orderings drift by a few
+        # accuracy the step counts of the two CG orderings drift by a few;
+        # above 8 nodes (multi-shift only) the seed, the node nearest the
+        # real axis, is not always the last system to converge, and its
+        # recurrence runs on until every shifted system has
         omax = max(int(s.iters.max()) for s in stats)
-        assert abs(info.cocg_max_last - omax) <= max(3, 0.06 * omax)
+        assert abs(info.cocg_max_last - omax) <= max(3, (0.06 if nc <= 8 else 0.15) * omax)
     finally:
         lib.rafeast_destroy(h)
 
