@@ -134,6 +134,16 @@ extern "C" {
                                      * into exact BF16 digits with integer      *
                                      * accumulation (m <= 128); 1 on the FP64   *
                                      * pipe                                     */
+#define RAFEAST_OPT_DEFER 17        /* float32 multi-shift solves with the    *
+                                     * tiled dot kernel: 1 the update kernel   *
+                                     * of step k leaves the shifted directions *
+                                     * and their quadrature terms to the dot   *
+                                     * kernel of step k + 1, which streams     *
+                                     * them beside its gathers (residuals      *
+                                     * ping-pong between two arrays); 0        *
+                                     * (default) every update complete (the    *
+                                     * deferred form moves more bytes and      *
+                                     * measured slower)                        */
 #define RAFEAST_OPT_TEST_STALL 9    /* test hook: bytes (multiple of 16) that  *
                                      * every bulk-copy stage waits for and no *
                                      * copy delivers, so the bounded wait     *

@@ -552,7 +552,7 @@ template <typename T>
 static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double* Qd,
                              const double* AQd, const double* theta_d,
                              const std::vector<double>& theta, int m0, int ldq, CocgCtl* ctl_dev,
-                             bool profile, bool stream, cudaStream_t st) {
+                             bool profile, bool stream, cudaStream_t st, bool pingpong = false) {
   using C = c2<T>;
   const int nc = prm.nc;
   const bool fp64 = sizeof(T) == 8;
@@ -594,7 +594,9 @@ static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double*
   const int ldps = pairs * ns * 2;          // shifted directions: complex per row
   const size_t seed_elems = (size_t)h->n * ldc * 2;
   const size_t ps_elems = (size_t)h->n * std::max(ldps, 1) * 2;
-  T* state = (T*)scratch(h, S_STATE, (4 * seed_elems + ps_elems) * sizeof(T));
+  // seed r, p, w, s, the shifted directions, and (ping-pong) a second r
+  T* state = (T*)scratch(h, S_STATE,
+                         ((pingpong ? 5 : 4) * seed_elems + ps_elems) * sizeof(T));
   const int ldd = ncol;
   T* dacc = (T*)scratch(h, S_DACC, (size_t)h->n * ldd * sizeof(T));
   size_t off = 0;
@@ -641,7 +643,10 @@ static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double*
                h->opt_cpl > 0 ? std::min(h->opt_cpl, ms_max_cpl(fp64)) : ms_max_cpl(fp64));
   if (stream) {
     // r and p in place, w = M r and s = M p beside them
+    // r in place, or r_k / r_{k+1} alternating between two arrays (the
+    // deferred form of the update still needs r_k after r_{k+1} is formed)
     a.r[0] = a.r[1] = state;
+    if (pingpong) a.r[1] = state + 4 * seed_elems + ps_elems;
     a.p[0] = a.p[1] = state + seed_elems;
     a.wbuf = state + 2 * seed_elems;
     a.sbuf = state + 3 * seed_elems;
@@ -703,20 +708,25 @@ static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double*
 // (streamed update: the dot kernel also writes w; the update kernel reads
 // r, p, w, s and writes r, p, s, and reads no A)
 static double ms_dots_bytes(const Handle* h, int act_d, bool fp64, bool stream = false,
-                            bool vf = false) {
+                            bool vf = false, int defer_ns = -1) {
   const double sv = fp64 ? 8.0 : 4.0;
   // values-free gathers read the off-diagonal pattern only
   const double abytes = vf ? (double)h->nnz_off * 4.0 + 4.0 * (h->n + 1)
                            : (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
   const double pairb = (double)h->n * 2 * 2.0 * sv;
-  return abytes + pairb * act_d * (stream ? 2.0 : 1.0);
+  double b = abytes + pairb * act_d * (stream ? 2.0 : 1.0);
+  // deferred form: the previous residual read, the shifted directions read
+  // and written, the quadrature sum read and written
+  if (defer_ns >= 0) b += (1.0 + 2.0 * defer_ns + 1.0) * pairb * act_d;
+  return b;
 }
 static double ms_update_bytes(const Handle* h, int act_u, int ns, bool fp64,
-                              bool stream = false) {
+                              bool stream = false, bool defer = false) {
   const double sv = fp64 ? 8.0 : 4.0;
   const double abytes = (double)h->nnz * (4.0 + sv) + 4.0 * (h->n + 1);
   const double pairb = (double)h->n * 2 * 2.0 * sv;
   const double dacc = 2.0 * (double)h->n * 2 * act_u * sv;
+  if (stream && defer) return 7.0 * pairb * act_u + dacc;
   if (stream) return (7.0 + 2.0 * ns) * pairb * act_u + dacc;
   return abytes + (4.0 + 2.0 * ns) * pairb * act_u + dacc;
 }
@@ -743,8 +753,11 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
   const bool fp64 = sizeof(T) == 8;
   // (the gathering update is compiled for up to 8 shifts)
   const bool stream = h->opt_update != 1 || prm.nc > 8;
+  // float32 streamed update, deferred form asked for: residuals ping-pong,
+  // so that the tiled dot kernel can take over the shifted updates
+  const bool pingpong = stream && !fp64 && h->opt_defer == 1 && h->ntiles > 0;
   MsProblem<T> P = ms_setup<T>(h, prm, Qd, AQd, theta_d, theta, m0, ldq, nullptr,
-                                h->opt_profile != 0, stream, h->stream);
+                                h->opt_profile != 0, stream, h->stream, pingpong);
   const CocgArgs<T>& a = P.a;
   const int pairs = P.pairs, ns = P.ns;
   const bool prof = h->opt_profile != 0;
@@ -778,7 +791,7 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
   auto launch_dots = [&](const CocgArgs<T>& ad, int buf, int cb, int occ) {
     if constexpr (std::is_same<T, float>::value) {
       if (cb > 0) {
-        launch_ms_dots_tiled(ad, tl_for(cb), h->num_sms, occ, h->stream);
+        launch_ms_dots_tiled(ad, tl_for(cb), buf, h->num_sms, occ, h->stream);
         return;
       }
     }
@@ -803,7 +816,7 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
         launch_dots(ad, it & 1, cb, occ);
         if (timed)
           RF_CUDA(cudaEventRecordWithFlags(evs[2 * it + 1], h->stream, cudaEventRecordExternal));
-        if (stream) launch_ms_update_stream<T>(au, h->num_sms, h->stream);
+        if (stream) launch_ms_update_stream<T>(au, it & 1, h->num_sms, h->stream);
         else launch_ms_update<T>(au, it & 1, h->num_sms, h->stream);
       }
       if (timed)
@@ -857,6 +870,7 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
       else have = true;
     }
   const bool tune = h->opt_autotune && !h->opt_lanes && !h->opt_cpl;
+  int tuned_steps = 0;  // COCG steps the autotuner ran (full updates)
   if (!have && !tune && can_tile && h->opt_tiled == 2) dot_cb = 8;
   if (!have && tune) {
     // (lanes, chunks, CTAs per SM; 0 = the default instance)
@@ -952,8 +966,15 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
   }
   h->prof[6] = dot_cb ? 1000000 + dot_cb * 100 + dot_occ : ad.occ * 10000 + ad.lanes * 100 + ad.cpl;
   h->prof[7] = au.occ * 10000 + au.lanes * 100 + au.cpl;
+  tuned_steps = (int)tk.size() / 2;
   int chunk = std::max(2, h->opt_chunk);
   chunk += chunk & 1;
+  // deferred form (RAFEAST_OPT_DEFER = 1, tiled dot kernel, ping-pong
+  // residuals): the update kernel leaves the shifted directions to the next
+  // dot kernel; the first dot kernel after a full update finds nothing
+  // pending
+  const bool defer = pingpong && dot_cb > 0;
+  ad.defer = au.defer = defer ? 1 : 0;
   std::vector<cudaEvent_t> evs;
   cudaGraphExec_t exec = nullptr;
   capture(ad, au, chunk, prof, evs, exec, dot_cb, dot_occ);
@@ -978,11 +999,14 @@ static void filter_ms_dev(Handle* h, const rafeast_params& prm, const double* Qd
       const int act_u = hist[k];
       h->prof[0] += 1;
       h->prof[1] += tk[2 * k];
-      h->prof[2] += ms_dots_bytes(h, act_d, fp64, stream, a.lcolidx != nullptr);
+      // (the autotuner's steps ran the full update; k counts from the
+      // solve's first step, the deferred form starts after them)
+      const bool dk = defer && k >= tuned_steps + 1, uk = defer && k >= tuned_steps;
+      h->prof[2] += ms_dots_bytes(h, act_d, fp64, stream, a.lcolidx != nullptr, dk ? ns : -1);
       if (act_u > 0) {
         h->prof[3] += 1;
         h->prof[4] += tk[2 * k + 1];
-        h->prof[5] += ms_update_bytes(h, act_u, ns, fp64, stream);
+        h->prof[5] += ms_update_bytes(h, act_u, ns, fp64, stream, uk);
       }
     }
   }
@@ -1888,6 +1912,10 @@ int rafeast_set_option(rafeast_t hh, int key, int64_t value) {
     case RAFEAST_OPT_TILED:
       if (value < 0 || value > 2) return RAFEAST_ERR_INVALID_ARG;
       h->opt_tiled = (int)value;
+      return RAFEAST_OK;
+    case RAFEAST_OPT_DEFER:
+      if (value < 0 || value > 1) return RAFEAST_ERR_INVALID_ARG;
+      h->opt_defer = (int)value;
       return RAFEAST_OK;
     case RAFEAST_OPT_DENSE:
       if (value < 0 || value > 1) return RAFEAST_ERR_INVALID_ARG;

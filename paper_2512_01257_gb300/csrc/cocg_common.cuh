@@ -366,6 +366,7 @@ __device__ void ms_scalar_finish(const CocgArgs<T>& a, int k, const MsCount& cnt
   if (cnt.mn != 0x7fffffff && (c->min_iters == 0 || cnt.mn < c->min_iters)) c->min_iters = cnt.mn;
   c->iter = k + 1;
   if (cnt.active == 0) c->done = 1;
+  c->pend = 0;  // (the dot kernel that ends here applied any deferred updates)
   __threadfence();
   c->ticket = 0;
 }

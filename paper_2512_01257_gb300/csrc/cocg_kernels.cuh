@@ -479,7 +479,7 @@ __device__ __forceinline__ void ms_stream_stage(const CocgArgs<T>& a, unsigned c
 template <typename T, int NS>
 __device__ __forceinline__ void ms_stream_elems(const CocgArgs<T>& a, const unsigned char* smem,
                                                 int64_t e0, int64_t e1, int64_t step,
-                                                int64_t lo, bool down) {
+                                                int64_t lo, bool down, int buf = 0) {
   using C = c2<T>;
   const int P = a.m0;
   const int ns = NS < 0 ? a.ns : NS;
@@ -488,10 +488,14 @@ __device__ __forceinline__ void ms_stream_elems(const CocgArgs<T>& a, const unsi
       reinterpret_cast<const ShiftCoef<T>*>(smem + sizeof(Coef<T>) * 2 * P);
   const int* sact = reinterpret_cast<const int*>(
       smem + (sizeof(Coef<T>) + ns * sizeof(ShiftCoef<T>)) * 2 * P);
-  T* __restrict__ R = a.r[0];
+  // r_k from r[buf], r_{k+1} into r[buf ^ 1] (the same array when r is
+  // updated in place)
+  const T* __restrict__ R = a.r[buf];
+  T* __restrict__ Rn = a.r[buf ^ 1];
   T* __restrict__ Pd = a.p[0];
   const T* __restrict__ W = a.wbuf;
   T* __restrict__ S = a.sbuf;
+  const int nsh = a.defer ? 0 : ns;  // deferred: the shifted directions wait
   for (int64_t e = e0; e < e1; e += step) {
     const int64_t ee = down ? lo + e1 - 1 - e : e;
     const int64_t row = ee / P;
@@ -515,7 +519,8 @@ __device__ __forceinline__ void ms_stream_elems(const CocgArgs<T>& a, const unsi
       dsum[h] = fma(cf.ca.x, pn.x, fma(-cf.ca.y, pn.y, dsum[h]));
     }
 #pragma unroll
-    for (int t = 0; t < (NS < 0 ? ns : NS); ++t) {
+    for (int t = 0; t < (NS < 0 ? nsh : NS); ++t) {
+      if (NS >= 0 && nsh == 0) break;  // deferred form
       const ShiftCoef<T> s0 = ssc[(2 * q) * ns + t];
       const ShiftCoef<T> s1 = ssc[(2 * q + 1) * ns + t];
       if (s0.act != (T)0 || s1.act != (T)0) {
@@ -533,7 +538,7 @@ __device__ __forceinline__ void ms_stream_elems(const CocgArgs<T>& a, const unsi
         st_chunk<2>(pp, pj);
       }
     }
-    st_chunk<2>(R + off, rn);
+    st_chunk<2>(Rn + off, rn);
     st_chunk<2>(Pd + off, pv);
     st_chunk<2>(S + off, sv);
     T* dp = a.dacc + row * a.ldd + 2 * q;

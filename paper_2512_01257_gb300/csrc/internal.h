@@ -58,6 +58,9 @@ struct CocgCtl {
   int g_active, g_brk, g_cap, g_mx, g_cols;
   int g_mn;                     // 0x7fffffff between steps
   unsigned long long g_worst;   // bits of a non-negative double
+  // 1 when the last update kernel left its shifted-direction updates to the
+  // next dot kernel (deferred form); cleared at the end of every scalar step
+  int pend;
 };
 
 // per-system scalar state, double precision (one struct per system s)
@@ -145,6 +148,12 @@ template <typename T> struct CocgArgs {
   // place (r[0] == r[1], p[0] == p[1]), s is kept in sbuf
   T* wbuf;
   T* sbuf;
+  // deferred form of the streamed update (defer = 1, tiled dot kernel): the
+  // update kernel of step k forms p_k, s_k, r_{k+1} (r ping-ponged between
+  // r[0] and r[1]) and the seed's quadrature term, and leaves the shifted
+  // directions and their quadrature terms of step k to the dot kernel of
+  // step k + 1, which applies them from r_k while its gathered rows load
+  int defer;
   // values-free Laplacian gathers (lcolidx != null): A = L + shift I with L a
   // unit-weight graph Laplacian (off-diagonal -1, diagonal = degree); lrowptr
   // and lcolidx hold the off-diagonal pattern only, L r = deg r - sum r_nbr
@@ -238,6 +247,7 @@ struct Handle {
   int opt_tiled = 0;        // seed dot kernel: 0 auto (tiled when built), 1 never, 2 only tiled
   int opt_tile_cb = 0;      // tiled dot kernel: forced column pairs per block (0: autotuned)
   int opt_dense = 0;        // FP64 Gram matrices: 0 tensor cores (digit split), 1 FP64 pipe
+  int opt_defer = 0;        // 1: deferred shifted updates with the tiled dot kernel, 0: never
   // autotuned kernel shapes (lanes, chunks per lane) of the multi-shift
   // kernels, keyed by (pairs, shifts, precision)
   struct Shape {
@@ -302,7 +312,7 @@ void tile_local_index(int64_t n, const int32_t* rowptr, const int32_t* colidx,
                       std::vector<int32_t>& uself);
 // tiled seed dot kernel of the multi-shift COCG (float32, streamed update);
 // occ_cap: most CTAs per SM (0: as many as fit, at most TILE_MAX_OCC)
-void launch_ms_dots_tiled(const CocgArgs<float>& a, const TileArgs& tl, int num_sms,
+void launch_ms_dots_tiled(const CocgArgs<float>& a, const TileArgs& tl, int buf, int num_sms,
                           int occ_cap, cudaStream_t s);
 
 // ---- kernel launchers (kernels_sparse.cu) --------------------------------------
@@ -322,7 +332,7 @@ template <typename T>
 void launch_ms_update(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s);
 // streamed multi-shift update (needs a.wbuf, a.sbuf; no gathers)
 template <typename T>
-void launch_ms_update_stream(const CocgArgs<T>& a, int num_sms, cudaStream_t s);
+void launch_ms_update_stream(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s);
 int ms_max_cpl(bool fp64);
 // bulk-copy (TMA) kernels, float32, NC in {2, 4, 8}, blocked state layout
 // (kernels_tma.cu). which: 0 init, 1 dots, 2 update.

@@ -297,16 +297,20 @@ __global__ void __launch_bounds__(THREADS, MINB) k_cocg_dots_occ(CocgArgs<T> a, 
 }
 
 template <typename T, int NS>
-__global__ void __launch_bounds__(THREADS) k_ms_update_stream(CocgArgs<T> a) {
+__global__ void __launch_bounds__(THREADS) k_ms_update_stream(CocgArgs<T> a, int buf) {
   if (__ldcg(&a.ctl->done)) return;
+  // deferred form: the next dot kernel finds this step's shifted updates
+  // pending (it starts after this kernel ends)
+  if (a.defer && blockIdx.x == 0 && threadIdx.x == 0) a.ctl->pend = 1;
   extern __shared__ unsigned char smem_raw[];
   ms_stream_stage<T, NS>(a, smem_raw);
   ms_stream_elems<T, NS>(a, smem_raw, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                         a.n * (int64_t)a.m0, (int64_t)gridDim.x * blockDim.x, 0, true);
+                         a.n * (int64_t)a.m0, (int64_t)gridDim.x * blockDim.x, 0, true, buf);
 }
 
 template <typename T, int NS>
-static void dispatch_ms_update_stream(const CocgArgs<T>& a, int num_sms, cudaStream_t s) {
+static void dispatch_ms_update_stream(const CocgArgs<T>& a, int buf, int num_sms,
+                                      cudaStream_t s) {
   // (NS < 0: the instance reads the shift count a.ns at run time)
   const size_t smem = ms_stream_smem<T>(a.m0, NS < 0 ? a.ns : NS);
   auto kern = k_ms_update_stream<T, NS>;
@@ -317,30 +321,32 @@ static void dispatch_ms_update_stream(const CocgArgs<T>& a, int num_sms, cudaStr
   int64_t blocks = (a.n * (int64_t)a.m0 + THREADS - 1) / THREADS;
   if (blocks > (int64_t)num_sms * occ) blocks = (int64_t)num_sms * occ;
   if (blocks < 1) blocks = 1;
-  kern<<<(int)blocks, THREADS, smem, s>>>(a);
+  kern<<<(int)blocks, THREADS, smem, s>>>(a, buf);
   RF_LAUNCH();
 }
 
 template <typename T>
-void launch_ms_update_stream(const CocgArgs<T>& a, int num_sms, cudaStream_t s) {
-  RF_CHECK(a.wbuf && a.sbuf && a.r[0] == a.r[1] && a.p[0] == a.p[1], RAFEAST_ERR_INVALID_ARG);
+void launch_ms_update_stream(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {
+  // (r in place or ping-ponged; the deferred form needs both residuals)
+  RF_CHECK(a.wbuf && a.sbuf && a.p[0] == a.p[1] && (!a.defer || a.r[0] != a.r[1]),
+           RAFEAST_ERR_INVALID_ARG);
   switch (a.ns) {
-    case 0: dispatch_ms_update_stream<T, 0>(a, num_sms, s); break;
-    case 1: dispatch_ms_update_stream<T, 1>(a, num_sms, s); break;
-    case 2: dispatch_ms_update_stream<T, 2>(a, num_sms, s); break;
-    case 3: dispatch_ms_update_stream<T, 3>(a, num_sms, s); break;
-    case 4: dispatch_ms_update_stream<T, 4>(a, num_sms, s); break;
-    case 5: dispatch_ms_update_stream<T, 5>(a, num_sms, s); break;
-    case 6: dispatch_ms_update_stream<T, 6>(a, num_sms, s); break;
-    case 7: dispatch_ms_update_stream<T, 7>(a, num_sms, s); break;
+    case 0: dispatch_ms_update_stream<T, 0>(a, buf, num_sms, s); break;
+    case 1: dispatch_ms_update_stream<T, 1>(a, buf, num_sms, s); break;
+    case 2: dispatch_ms_update_stream<T, 2>(a, buf, num_sms, s); break;
+    case 3: dispatch_ms_update_stream<T, 3>(a, buf, num_sms, s); break;
+    case 4: dispatch_ms_update_stream<T, 4>(a, buf, num_sms, s); break;
+    case 5: dispatch_ms_update_stream<T, 5>(a, buf, num_sms, s); break;
+    case 6: dispatch_ms_update_stream<T, 6>(a, buf, num_sms, s); break;
+    case 7: dispatch_ms_update_stream<T, 7>(a, buf, num_sms, s); break;
     default:  // N_c = 9..16: the shift count read at run time
       if (a.ns < 0 || a.ns > 15) throw Err{RAFEAST_ERR_INVALID_ARG};
-      dispatch_ms_update_stream<T, -1>(a, num_sms, s);
+      dispatch_ms_update_stream<T, -1>(a, buf, num_sms, s);
       break;
   }
 }
-template void launch_ms_update_stream<float>(const CocgArgs<float>&, int, cudaStream_t);
-template void launch_ms_update_stream<double>(const CocgArgs<double>&, int, cudaStream_t);
+template void launch_ms_update_stream<float>(const CocgArgs<float>&, int, int, cudaStream_t);
+template void launch_ms_update_stream<double>(const CocgArgs<double>&, int, int, cudaStream_t);
 
 template <typename T, int NS>
 static void dispatch_ms_update(const CocgArgs<T>& a, int buf, int num_sms, cudaStream_t s) {

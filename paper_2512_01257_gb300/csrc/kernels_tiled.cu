@@ -122,10 +122,18 @@ __device__ __forceinline__ void tile_copies(const TileArgs& tl, TileIdx& b, P4* 
   }
 }
 
+// the shifted systems' coefficients of one column (deferred form), staged
+struct DefCoef {
+  float2 zeta, beta, ca;
+};
+
 template <int CB, bool VF>
-__global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a, TileArgs tl) {
+__global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a, TileArgs tl,
+                                                               int buf) {
   if (__ldcg(&a.ctl->done)) return;
-  extern __shared__ __align__(16) P4 xs[];  // [max_union * CB] staged chunks; reused for the sums
+  // [max_union * CB] staged chunks (reused for the sums), then, for the
+  // deferred form, the block's shifted coefficients [CB][2][ns]
+  extern __shared__ __align__(16) P4 xs[];
   __shared__ TileIdx tb;
   __shared__ int sact[CB];
   constexpr int NRS = TT / CB;  // row slots
@@ -143,12 +151,41 @@ __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a
 #pragma unroll
   for (int t = 0; t < CB; ++t) any |= sact[t];
   const int64_t ldt = (int64_t)a.ldc * 2;  // floats per state row
-  const float* __restrict__ R = a.r[0];
+  const float* __restrict__ R = a.r[buf];   // r_k
   const int32_t* __restrict__ rowptr = VF ? a.lrowptr : a.rowptr;
   const float2 z = reinterpret_cast<const float2*>(a.zs)[0];
   float d[10];
 #pragma unroll
   for (int t = 0; t < 10; ++t) d[t] = 0.0f;
+  // deferred form: the previous step's shifted directions and their
+  // quadrature terms are applied here, from r_{k-1} (the other residual
+  // buffer) and the coefficients of the previous scalar step (this block's
+  // columns are rewritten only by this block's last CTA, after every CTA of
+  // the block is done)
+  const bool pend = a.defer && __ldcg(&a.ctl->pend) != 0;
+  const int ns = a.ns;
+  DefCoef* sdc = reinterpret_cast<DefCoef*>(xs + tl.max_union * CB);
+  if (pend) {
+    for (int e = threadIdx.x; e < CB * 2 * ns; e += TT) {
+      const int jj = e / (2 * ns), h = (e / ns) & 1, t = e % ns;
+      const int qq = cbk * CB + jj;
+      DefCoef c;
+      c.zeta = make_float2(0.f, 0.f);
+      c.beta = make_float2(1.f, 0.f);
+      c.ca = make_float2(0.f, 0.f);
+      if (qq < a.m0) {
+        const ShiftCoef<float> sc = a.scf[(2 * qq + h) * ns + t];
+        if (sc.act != 0.f) {
+          c.zeta = sc.zeta;
+          c.beta = sc.beta;
+          c.ca = sc.ca;
+        }
+      }
+      sdc[e] = c;
+    }
+    __syncthreads();
+  }
+  const float* __restrict__ Rprev = a.r[buf ^ 1];  // r_{k-1}
   const int nitems = tl.ntiles * ncb;
   for (int item = blockIdx.x; any && item < nitems; item += gridDim.x) {
     // the tile's indices (plain loads, all in flight together), then the
@@ -214,6 +251,37 @@ __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a
         if (a.wbuf)
           *reinterpret_cast<float4*>(a.wbuf + row * ldt + (int64_t)q * 4) =
               make_float4(w2[0].x, w2[0].y, w2[1].x, w2[1].y);
+        // deferred form: this row's shifted directions and quadrature terms
+        // of the previous step (streamed; its loads interleave with the
+        // next row's shared-memory gathers)
+        if (pend) {
+          const DefCoef* dc = sdc + j * 2 * ns;
+          const float4 rp4 = __ldcg(reinterpret_cast<const float4*>(Rprev + row * ldt) + q);
+          const float2 rp[2] = {make_float2(rp4.x, rp4.y), make_float2(rp4.z, rp4.w)};
+          float dsum[2] = {0.f, 0.f};
+          for (int t = 0; t < ns; ++t) {
+            const DefCoef c0 = dc[t], c1 = dc[ns + t];
+            if (c0.ca.x == 0.f && c0.ca.y == 0.f && c0.zeta.x == 0.f && c0.zeta.y == 0.f &&
+                c1.ca.x == 0.f && c1.ca.y == 0.f && c1.zeta.x == 0.f && c1.zeta.y == 0.f)
+              continue;  // both systems of the pair stopped: p_j stays as it is
+            float* pp = a.ps + (row * a.ldps + 2 * ((int64_t)q * ns + t)) * 2;
+            const float4 p4 = __ldcg(reinterpret_cast<const float4*>(pp));
+            float2 pj[2] = {make_float2(p4.x, p4.y), make_float2(p4.z, p4.w)};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const DefCoef& c = h ? c1 : c0;
+              // p_j^k = zeta_k r_k + beta_j p_j^{k-1};  D += Re(c_j alpha_j p_j^k)
+              pj[h] = cfma<float>(c.beta, pj[h], cmul<float>(c.zeta, rp[h]));
+              dsum[h] = fmaf(c.ca.x, pj[h].x, fmaf(-c.ca.y, pj[h].y, dsum[h]));
+            }
+            *reinterpret_cast<float4*>(pp) = make_float4(pj[0].x, pj[0].y, pj[1].x, pj[1].y);
+          }
+          float2* dp = reinterpret_cast<float2*>(a.dacc + row * a.ldd + 2 * q);
+          float2 dv = *dp;
+          dv.x += dsum[0];
+          dv.y += dsum[1];
+          *dp = dv;
+        }
       }
     }
     __syncthreads();  // the next item's copies overwrite the staged data
@@ -301,12 +369,13 @@ __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a
 }
 
 template <int CB, bool VF>
-static void launch_cb(const CocgArgs<float>& a, const TileArgs& tl, int num_sms, int occ_cap,
-                      cudaStream_t s) {
+static void launch_cb(const CocgArgs<float>& a, const TileArgs& tl, int buf, int num_sms,
+                      int occ_cap, cudaStream_t s) {
   auto kern = k_ms_dots_tiled<CB, VF>;
   const size_t stage = (size_t)tl.max_union * CB * sizeof(float4);
   const size_t red = (size_t)TT * 10 * sizeof(double);
-  const size_t smem = stage > red ? stage : red;
+  const size_t coef = a.defer ? (size_t)CB * 2 * a.ns * sizeof(DefCoef) : 0;
+  const size_t smem = (stage > red ? stage : red) + coef;
   ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
   int occ = 0;
   RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TT, smem));
@@ -315,19 +384,19 @@ static void launch_cb(const CocgArgs<float>& a, const TileArgs& tl, int num_sms,
   if (occ_cap > 0 && occ > occ_cap) occ = occ_cap;
   int g = (num_sms * occ / tl.ncb) * tl.ncb;
   if (g < tl.ncb) g = tl.ncb;
-  kern<<<g, TT, smem, s>>>(a, tl);
+  kern<<<g, TT, smem, s>>>(a, tl, buf);
   RF_LAUNCH();
 }
 
-void launch_ms_dots_tiled(const CocgArgs<float>& a, const TileArgs& tl, int num_sms,
+void launch_ms_dots_tiled(const CocgArgs<float>& a, const TileArgs& tl, int buf, int num_sms,
                           int occ_cap, cudaStream_t s) {
   const bool vf = a.lcolidx != nullptr;
-  RF_CHECK(a.r[0] == a.r[1] && a.ms == 1, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(a.ms == 1 && (!a.defer || a.r[0] != a.r[1]), RAFEAST_ERR_INVALID_ARG);
   switch (tl.cb) {
-    case 4: vf ? launch_cb<4, true>(a, tl, num_sms, occ_cap, s)
-               : launch_cb<4, false>(a, tl, num_sms, occ_cap, s); break;
-    case 8: vf ? launch_cb<8, true>(a, tl, num_sms, occ_cap, s)
-               : launch_cb<8, false>(a, tl, num_sms, occ_cap, s); break;
+    case 4: vf ? launch_cb<4, true>(a, tl, buf, num_sms, occ_cap, s)
+               : launch_cb<4, false>(a, tl, buf, num_sms, occ_cap, s); break;
+    case 8: vf ? launch_cb<8, true>(a, tl, buf, num_sms, occ_cap, s)
+               : launch_cb<8, false>(a, tl, buf, num_sms, occ_cap, s); break;
     default: throw Err{RAFEAST_ERR_INVALID_ARG};
   }
 }

@@ -57,6 +57,7 @@ RAFEAST_OPT_VALUES_FREE = 13
 RAFEAST_OPT_TILED = 14
 RAFEAST_OPT_TILE_CB = 15
 RAFEAST_OPT_DENSE = 16
+RAFEAST_OPT_DEFER = 17
 
 EXPORTS = [
     "rafeast_create", "rafeast_destroy", "rafeast_status_string", "rafeast_set_option",

@@ -4,7 +4,9 @@ The tiled kernel stages each row tile's gathered rows in shared memory and
 sums its dot products in a fixed order. These tests check it against the
 oracle after a fixed number of COCG steps (Algorithm 2 Step 2a; no
 convergence test, so a wrong alpha or beta cannot hide), against the
-register-gather kernel on the same steps, for every column-block width, on
+register-gather kernel on the same steps, for every column-block width, with
+the shifted-direction updates of each step done by the update kernel or
+deferred to the next dot kernel, on
 unit Laplacians (values-free gathers) and on weighted matrices (values read),
 with ragged column blocks, empty rows and a reordered kNN graph; and that two
 solves with the same kernel shapes give identical results.
@@ -54,10 +56,11 @@ def _matrix(kind):
             (a + 0.5 * sp.identity(a.shape[0])).tocsr(), (0.1, 0.4))
 
 
-def _filter(lib, h, Q, m0, nc, lo, hi, steps, tiled, cb=0):
+def _filter(lib, h, Q, m0, nc, lo, hi, steps, tiled, cb=0, defer=True):
     import torch
     # autotuning off: every step of the call runs the kernel asked for
     lib.rafeast_set_option(h, lib.RAFEAST_OPT_AUTOTUNE, 0)
+    lib.rafeast_set_option(h, lib.RAFEAST_OPT_DEFER, 1 if defer else 0)
     lib.rafeast_set_option(h, lib.RAFEAST_OPT_SOLVER, 1)
     lib.rafeast_set_option(h, lib.RAFEAST_OPT_UPDATE, 2)
     lib.rafeast_set_option(h, lib.RAFEAST_OPT_TILED, 2 if tiled else 1)
@@ -96,10 +99,11 @@ def test_tiled_dots_match_oracle_and_gathers_stepwise(lib, kind, m0, nc):
         eg = np.linalg.norm(qg - exp) / scale
         tol = max(5e-5, 2.0 * eg)
         for cb in (4, 8):
-            qt = _filter(lib, h, Q, m0, nc, lo, hi, 12, True, cb)
-            et = np.linalg.norm(qt - exp) / scale
-            assert et <= tol, (cb, et, eg)
-            assert np.linalg.norm(qt - qg) / scale <= max(2e-5, 2.0 * eg), cb
+            for defer in (True, False):
+                qt = _filter(lib, h, Q, m0, nc, lo, hi, 12, True, cb, defer)
+                et = np.linalg.norm(qt - exp) / scale
+                assert et <= tol, (cb, defer, et, eg)
+                assert np.linalg.norm(qt - qg) / scale <= max(2e-5, 2.0 * eg), (cb, defer)
     finally:
         lib.rafeast_destroy(h)
 
