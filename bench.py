@@ -87,6 +87,21 @@ def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
     """Units of all replicas per second over the slowest rank's time."""
     return units_per_rank * world / (ms / 1e3)
 
+
+def sharded_rate(units_total: float, ms: float) -> float:
+    """Units the ranks processed together per second over the slowest rank's
+    time (a sharded run: every unit is shared out, not repeated)."""
+    return units_total / (ms / 1e3)
+
+
+def my_instances(costs, world: int, rank: int, R=None):
+    """Indices of the problems this rank solves (longest first to the least
+    loaded rank, rafeast_partition_instances); all of them at world = 1."""
+    if world == 1:
+        return list(range(len(costs)))
+    owner = R.rafeast_partition_instances(costs, world)
+    return [t for t in range(len(costs)) if owner[t] == rank]
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -330,6 +345,12 @@ def run_batched(args):
     S = CF.SBM_SOLVE
     gold = CF.load_golden()["sbm64"]["instances"]
     insts = CF.sbm_instances()
+    total = len(insts)
+    # N ranks: each solves its share of the problems (cost nnz x m0), no
+    # exchange between ranks
+    mine = my_instances([g["nnz"] * i["m0"] for i, g in zip(insts, gold)], world, rank, R)
+    insts = [insts[t] for t in mine]
+    gold = [gold[t] for t in mine]
     t_gen = time.perf_counter()
     laps = [CF.make_sbm(i) for i in insts]
     t_gen = time.perf_counter() - t_gen
@@ -402,10 +423,21 @@ def run_batched(args):
             continue
         worst = max(worst, float(np.max(np.abs(ev - ref) / np.abs(ref))))
     infos = last["info"]
+    n_conv = sum(1 for x in last["st"] if x == R.RAFEAST_OK)
+    it_max = max(i.outer_iters for i in infos)
+    it_sum = sum(i.outer_iters for i in infos)
+    if dist:
+        agg = torch.tensor([worst, 0.0 if found_all else 1.0, float(it_max)], dtype=torch.float64,
+                           device=dev)
+        dist.all_reduce(agg, op=dist.ReduceOp.MAX)
+        tot = torch.tensor([float(n_conv), float(it_sum)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        worst, found_all, it_max = float(agg[0]), agg[1].item() == 0.0, int(agg[2])
+        n_conv, it_sum = int(tot[0]), float(tot[1])
     # the same 64 problems one at a time (rafeast_solve each, same settings)
     loop_ms, loop_kernels = None, None
     trace = R.rafeast_profile_history(hs[0])
-    if not args.no_loop:
+    if not args.no_loop and world == 1:
         for h in hs:
             R.rafeast_set_option(h, R.RAFEAST_OPT_PROFILE, 1)
             R.rafeast_profile(h, reset=True)
@@ -447,10 +479,10 @@ def run_batched(args):
                                  "ms_per_launch": prof[f"{other}_ms"] / max(prof[f"{other}_launches"], 1)},
                 "share_of_step": (prof["update_ms"] + prof["dots_ms"]) / ms}
     ns = [lap.n for lap in laps]
-    value = whole_job_rate(args.steps * cnt, world, ms)
+    value = sharded_rate(args.steps * total, ms)
     line = {"metric": METRIC, "value": value, "unit": "problems/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "time_to_solution_s": ms_step / 1e3, "higher_is_better": True, "scaling": "weak",
+            "time_to_solution_s": ms_step / 1e3, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32",
             "precision": "mixed: f32 shifted solves and SpMM; f64 Gram, Cholesky-QR, "
                          "Rayleigh-Ritz, residuals",
@@ -459,17 +491,19 @@ def run_batched(args):
                                    "log-uniform in [2000, 300000], 4-16 blocks, p_in=20/n_block, "
                                    "p_out=1/n, k=blocks+8, m0=ceil(1.5k), N_c=2 (ellipse ratio "
                                    "0.3), batched",
-                       "count": cnt, "sum_n": int(sum(ns)), "min_n": min(ns), "max_n": max(ns),
+                       "count": total, "sum_n": int(sum(ns)), "min_n": min(ns), "max_n": max(ns),
                        "sum_nnz": int(sum(lap.nnz for lap in laps)), "nc": S["nc"],
+                       "parallelism": (f"instances sharded over {world} ranks by nnz x m0 "
+                                       "(no exchange); n and nnz figures are rank 0's share"
+                                       if world > 1 else "one GPU"),
                        "p": S["p"], "q": S["q"], "solve_tol": S["solve_tol"],
                        "outer_tol": S["outer_tol"], "max_inner": S["max_inner"],
                        "l2": "inputs larger than L2 (no flush): COCG state of all instances"},
             "parity": {"max_eig_relerr_vs_lanczos": worst if found_all else None,
                        "all_found": found_all, "gate": 1e-8,
-                       "converged": sum(1 for x in last["st"] if x == R.RAFEAST_OK),
-                       "count": cnt},
-            "outer_iters_max": max(i.outer_iters for i in infos),
-            "outer_iters_mean": statistics.mean(i.outer_iters for i in infos),
+                       "converged": n_conv, "count": total},
+            "outer_iters_max": it_max,
+            "outer_iters_mean": it_sum / total,
             "per_instance_loop_ms": loop_ms, "per_instance_loop_kernels": loop_kernels,
             "batched_kernels": {"dots_ms": prof["dots_ms"] / args.steps,
                                 "update_ms": prof["update_ms"] / args.steps,
@@ -512,7 +546,11 @@ def run_batched(args):
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         el = max_over_ranks(el, dist, dev)
-        line["e2e"] = {"value": cnt * world / el, "unit": "problems/s",
+        if dist:
+            bt = torch.tensor([float(bi), float(bo)], dtype=torch.float64, device=dev)
+            dist.all_reduce(bt, op=dist.ReduceOp.SUM)
+            bi, bo = int(bt[0]), int(bt[1])
+        line["e2e"] = {"value": total / el, "unit": "problems/s",
                        "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": 1,
                        "includes": "rafeast_create of all 64 from pinned host CSR, warmstarts, "
                                    "batched solve, copy of eigenpairs to host"}
@@ -734,6 +772,10 @@ def main():
                     help="also time plain FEAST in FP64 (random start, N_c = 8, COCG to 1e-10; "
                          "about five minutes on knn200k)")
     ap.add_argument("--trace", default="", help="sbm64: write the batched per-step trace here")
+    ap.add_argument("--shard", default="columns", choices=["columns", "shifts", "replicas"],
+                    help="N > 1, single-problem workloads: share one solve out by subspace "
+                         "columns or quadrature nodes (one all-reduce per outer iteration), "
+                         "or run a whole replica per rank")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -776,6 +818,17 @@ def main():
                              R.RAFEAST_START_SUBSPACE)
 
     infos = []
+    # N ranks: one solve shared out over the ranks (rafeast_solve_sharded:
+    # columns of the subspace, or quadrature nodes), one all-reduce of the
+    # filtered block per outer iteration; or whole replicas (--shard replicas)
+    sharded = world > 1 and args.shard != "replicas"
+    shard_mode = R.RAFEAST_SHARD_SHIFTS if args.shard == "shifts" else R.RAFEAST_SHARD_COLUMNS
+    sum_fn = R.allreduce_sum() if sharded else None
+
+    def solve(hh, prm, ev, vec, res):
+        if sharded:
+            return R.rafeast_solve_sharded(hh, prm, shard_mode, rank, world, sum_fn, ev, vec, res)
+        return R.rafeast_solve(hh, prm, ev, vec, res)
 
     # the RGG workloads stop at the paper's iteration limit (status 2 is the
     # expected outcome there); the others must converge
@@ -790,7 +843,7 @@ def main():
         R.rafeast_warmstart(h, lmin, lmax, m0, cfg.p, cfg.q, cfg.seed)
         w1.record(torch.cuda.current_stream())
         ws_events.append((w0, w1))
-        st, mf, info = R.rafeast_solve(h, params(p), evals, evecs, resid)
+        st, mf, info = solve(h, params(p), evals, evecs, resid)
         if st not in ok_status:
             raise RuntimeError(f"solve status {st}: {info.as_dict()}")
         infos.append((mf, info))
@@ -829,7 +882,7 @@ def main():
     R.rafeast_set_option(h, R.RAFEAST_OPT_PROFILE, 0)
     ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
-    value = whole_job_rate(args.steps, world, ms)
+    value = sharded_rate(args.steps, ms) if sharded else whole_job_rate(args.steps, world, ms)
     # parity of the last timed step against the stored ARPACK eigenvalues
     mf, info = infos[-1]
     ev = evals.cpu().numpy()[:mf]
@@ -889,11 +942,16 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "time_to_solution_s": ms_step / 1e3, "higher_is_better": True, "scaling": "weak",
+            "time_to_solution_s": ms_step / 1e3, "higher_is_better": True,
+            "scaling": "weak" if args.shard == "replicas" else "strong",
             "vs_baseline": None, "dtype": "f32" if prec == R.RAFEAST_MIXED else "f64",
             "precision": ("mixed: f32 shifted solves and SpMM; f64 Gram, Cholesky-QR, "
                           "Rayleigh-Ritz, residuals") if prec == R.RAFEAST_MIXED else "f64",
-            "data": "synthetic (seeded generator, no dataset)", "config": _config(key),
+            "data": "synthetic (seeded generator, no dataset)",
+            "config": dict(_config(key), parallelism=(
+                f"one solve sharded over {world} ranks by {args.shard} (one all-reduce of the "
+                "n x m0 filtered block per outer iteration)" if sharded else
+                f"{world} replicas" if world > 1 else "one GPU")),
             "parity": {"max_eig_relerr_vs_arpack": relerr, "m_found": mf, "count": g["count"],
                        "gate": 1e-8 if prec == R.RAFEAST_MIXED else 1e-10},
             "outer_iters": info.outer_iters, "cocg_iters_total": info.cocg_iters_total,
@@ -977,7 +1035,7 @@ def main():
             hh = R.rafeast_create(hrp.numpy(), hci.numpy(), hva.numpy(), lap.shift)
             try:
                 R.rafeast_warmstart(hh, lmin, lmax, m0, cfg.p, cfg.q, cfg.seed)
-                st, _, _ = R.rafeast_solve(hh, params(prec), oev, ove, ore)
+                st, _, _ = solve(hh, params(prec), oev, ove, ore)
                 assert st == R.RAFEAST_OK
             finally:
                 R.rafeast_destroy(hh)
@@ -992,7 +1050,8 @@ def main():
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         el = max_over_ranks(el, dist, dev)
-        line["e2e"] = {"value": ek * world / el, "unit": "solves/s", "h2d_bytes_per_step": bi,
+        line["e2e"] = {"value": ek / el if sharded else ek * world / el, "unit": "solves/s",
+                       "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo, "steps": ek,
                        "includes": "rafeast_create from pinned host CSR (row reorder on the "
                                    "host), warmstart, solve, copy of eigenpairs to host"}

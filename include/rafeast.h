@@ -55,6 +55,7 @@ extern "C" {
 #define RAFEAST_ERR_NOT_READY (-7)   /* e.g. START_SUBSPACE with no subspace  */
 #define RAFEAST_ERR_CHOLESKY (-8)    /* Cholesky-QR failed even when shifted  */
 #define RAFEAST_ERR_NO_DEVICE (-9)
+#define RAFEAST_ERR_EXCHANGE (-10)   /* a sharded solve's sum callback failed */
 
 /* ---- enums --------------------------------------------------------------- */
 #define RAFEAST_FP64 0   /* every step in double                              */
@@ -407,6 +408,71 @@ int rafeast_solve_batched(int count, rafeast_t const* hs,
                           double* const* evals, double* const* evecs,
                           double* const* resid, int outputs_on_device,
                           rafeast_info* infos, int* statuses);
+
+/* ---- sharding over ranks (one process and one GPU per rank) ----------------
+ * The filter step of the outer loop (Algorithm 1, Algorithm 2 Phase 2:
+ * Q~ = sum_j w_j (z_j I - A)^{-1} Q, Eq. 2) splits into independent shifted
+ * solves. A sharded solve gives each rank a share of them and adds the
+ * ranks' partial blocks with one sum over ranks per outer iteration; every
+ * rank then runs the same orthonormalisation, Rayleigh-Ritz and residual
+ * steps on the same block. The paper runs on one CPU thread and has no
+ * counterpart: this is the GPU layout of its independent solves. */
+#define RAFEAST_SHARD_COLUMNS 0 /* each rank filters a range of Q's columns    *
+                                 * (whole column pairs) with all N_c nodes;     *
+                                 * the other columns of its block are zero, so *
+                                 * the sum over ranks is exact                  */
+#define RAFEAST_SHARD_SHIFTS 1  /* each rank filters every column with a range *
+                                 * of the N_c nodes; the sum over ranks adds    *
+                                 * partial quadrature sums (rounding differs   *
+                                 * from one rank's sum in the last bits). With *
+                                 * the multi-shift solver every rank runs the  *
+                                 * seed recurrence of its nodes: the sparse    *
+                                 * products are not divided, only the shifted  *
+                                 * updates                                     */
+
+/* [*lo, *hi) = rank's share in a world of `world` ranks: columns of m0 for
+ * RAFEAST_SHARD_COLUMNS (pairs split as evenly as they go, rank order), or
+ * quadrature nodes of nc for RAFEAST_SHARD_SHIFTS (nc * rank / world ..).
+ * A share can be empty (more ranks than pairs or nodes). Host only; -1 for
+ * a bad mode, rank, world, m0 or nc. */
+int rafeast_shard_range(int mode, int m0, int nc, int rank, int world, int* lo, int* hi);
+
+/* Instance sharding of many independent problems (the batched workload):
+ * owner[i] = the rank (0 .. world-1) that solves problem i, chosen longest
+ * first: by decreasing cost[i] (ties: lower index first) each problem goes
+ * to the rank with the least cost so far (ties: the lower rank). Host only,
+ * deterministic, so every rank computes the same owners; cost is any
+ * non-negative work estimate (e.g. nnz). -1 for count < 0, world < 1, a
+ * negative cost or null arrays with count > 0. */
+int rafeast_partition_instances(int count, const int64_t* cost, int world, int32_t* owner);
+
+/* The caller's sum over ranks: on return, buf (count doubles, device memory
+ * of the handle's device) must hold on every rank the element-wise sum of
+ * all ranks' buf, with the caller's device work finished. The library has
+ * synchronised its stream before the call, and it resumes its own work on
+ * that stream afterwards. Every rank must add in the same order, so that
+ * all ranks hold the same bits (an NCCL or gloo all-reduce does). Return 0,
+ * or non-zero on failure (the solve then returns RAFEAST_ERR_EXCHANGE). */
+typedef int (*rafeast_sum_fn)(void* ctx, double* buf, int64_t count);
+
+/* rafeast_solve on rank `rank` of `world`, each rank with its own handle of
+ * the same matrix (same CSR, create flags and options), the same params and
+ * the same starting subspace (after the same rafeast_warmstart or
+ * set_subspace; START_RANDOM draws the same block on every rank). Per outer
+ * iteration the rank filters its share (rafeast_shard_range of `mode`) into
+ * an n x m0 block, zero elsewhere, and calls sum(ctx, block, n * ldq) once,
+ * ldq = m0 rounded up to even; after the Rayleigh-Ritz step it calls
+ * sum(ctx, flag, 1) with flag 1.0 when the rank's residual test passed: the
+ * loop stops when every rank passed, so that all ranks make the same number
+ * of calls. Each rank ends with the whole result (outputs as rafeast_solve);
+ * info counts this rank's COCG steps. world = 1 is rafeast_solve (no call of
+ * sum, which may be null). Returns as rafeast_solve, RAFEAST_ERR_EXCHANGE
+ * when sum failed, -1 for a bad mode, rank or world (or world > 1 with a null
+ * sum). */
+int rafeast_solve_sharded(rafeast_t h, const rafeast_params* prm, int mode, int rank,
+                          int world, rafeast_sum_fn sum, void* ctx, int* m_found,
+                          double* evals, double* evecs, double* resid, int outputs_on_device,
+                          rafeast_info* info);
 
 #ifdef __cplusplus
 }

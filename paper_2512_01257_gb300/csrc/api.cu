@@ -314,16 +314,27 @@ struct FilterStats {
   int iters_max = 0, iters_min = 0, breakdown = 0, capped = 0;
 };
 
+// a shift-sharded filter sums over the nodes [shard_j0, shard_j1) only: the
+// partial filtered blocks of all ranks add up to the N_c-node sum (Eq. 2)
+static void shard_nodes(const Handle* h, std::vector<double>& zr, std::vector<double>& zi,
+                        std::vector<double>& wr, std::vector<double>& wi) {
+  if (h->shard_j1 < 0) return;
+  const int nc = (int)zr.size();
+  const int j0 = std::max(0, std::min(h->shard_j0, nc)), j1 = std::max(j0, std::min(h->shard_j1, nc));
+  for (auto* v : {&zr, &zi, &wr, &wi}) *v = std::vector<double>(v->begin() + j0, v->begin() + j1);
+}
+
 template <typename T>
 static void filter_dev(Handle* h, const rafeast_params& prm, const double* Qd, const double* AQd,
                        const double* theta_d, const std::vector<double>& theta, int m0, int ldq,
                        double* Qt, FilterStats& fs) {
   using C = c2<T>;
-  const int nc = prm.nc;
-  const int NC = nc_pad(nc);
   const bool fp64 = sizeof(T) == 8;
   std::vector<double> zr, zi, wr, wi;
-  quadrature_nodes(prm.lmin, prm.lmax, nc, prm.ellipse_ratio, zr, zi, wr, wi);
+  quadrature_nodes(prm.lmin, prm.lmax, prm.nc, prm.ellipse_ratio, zr, zi, wr, wi);
+  shard_nodes(h, zr, zi, wr, wi);
+  const int nc = (int)zr.size();
+  const int NC = nc_pad(nc);
   const int nsys = m0 * NC;
   const bool corr = prm.solve_form == RAFEAST_FORM_CORRECTION;
   // host-side small tables
@@ -554,10 +565,11 @@ static MsProblem<T> ms_setup(Handle* h, const rafeast_params& prm, const double*
                              const std::vector<double>& theta, int m0, int ldq, CocgCtl* ctl_dev,
                              bool profile, bool stream, cudaStream_t st, bool pingpong = false) {
   using C = c2<T>;
-  const int nc = prm.nc;
   const bool fp64 = sizeof(T) == 8;
   std::vector<double> zr, zi, wr, wi;
-  quadrature_nodes(prm.lmin, prm.lmax, nc, prm.ellipse_ratio, zr, zi, wr, wi);
+  quadrature_nodes(prm.lmin, prm.lmax, prm.nc, prm.ellipse_ratio, zr, zi, wr, wi);
+  shard_nodes(h, zr, zi, wr, wi);
+  const int nc = (int)zr.size();
   int seed = 0;
   for (int j = 1; j < nc; ++j)
     if (zi[j] < zi[seed]) seed = j;
@@ -1583,6 +1595,7 @@ const char* rafeast_status_string(int s) {
     case RAFEAST_ERR_NOT_READY: return "no subspace in the handle";
     case RAFEAST_ERR_CHOLESKY: return "Cholesky-QR failed (rank-deficient block)";
     case RAFEAST_ERR_NO_DEVICE: return "no CUDA device";
+    case RAFEAST_ERR_EXCHANGE: return "the sharded solve's sum callback failed";
     default: return "unknown status";
   }
 }
@@ -2388,6 +2401,123 @@ int rafeast_solve(rafeast_t hh, const rafeast_params* prm, int* m_found, double*
     r.cocg_total += r.fs.iters_max;
     RF_CUDA(cudaEventRecord(r.ev[3], h->stream));
     if (solve_outer_tail(r)) break;
+  }
+  if (r.it > prm->max_outer) r.it = prm->max_outer;
+  const int status = solve_finish(r, m_found, evals, evecs, resid, outputs_on_device, info);
+  scope.finish();
+  return status;
+  API_END
+}
+
+int rafeast_shard_range(int mode, int m0, int nc, int rank, int world, int* lo, int* hi) {
+  if (!lo || !hi || world < 1 || rank < 0 || rank >= world || m0 < 1 || nc < 1)
+    return RAFEAST_ERR_INVALID_ARG;
+  if (mode == RAFEAST_SHARD_COLUMNS) {
+    // whole column pairs, so that every rank's block starts 16-byte aligned
+    const int64_t pairs = (m0 + 1) / 2;
+    *lo = (int)std::min<int64_t>(m0, 2 * (pairs * rank / world));
+    *hi = (int)std::min<int64_t>(m0, 2 * (pairs * (rank + 1) / world));
+  } else if (mode == RAFEAST_SHARD_SHIFTS) {
+    *lo = (int)((int64_t)nc * rank / world);
+    *hi = (int)((int64_t)nc * (rank + 1) / world);
+  } else {
+    return RAFEAST_ERR_INVALID_ARG;
+  }
+  return RAFEAST_OK;
+}
+
+int rafeast_partition_instances(int count, const int64_t* cost, int world, int32_t* owner) {
+  if (count < 0 || world < 1 || (count > 0 && (!cost || !owner))) return RAFEAST_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i)
+    if (cost[i] < 0) return RAFEAST_ERR_INVALID_ARG;
+  // longest processing time first: largest cost to the least loaded rank
+  // (ties: the lower instance index first, the lower rank)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int64_t> load(world, 0);
+  for (int i : order) {
+    int r = 0;
+    for (int q = 1; q < world; ++q)
+      if (load[q] < load[r]) r = q;
+    owner[i] = r;
+    load[r] += cost[i];
+  }
+  return RAFEAST_OK;
+}
+
+int rafeast_solve_sharded(rafeast_t hh, const rafeast_params* prm, int mode, int rank, int world,
+                          rafeast_sum_fn sum, void* ctx, int* m_found, double* evals,
+                          double* evecs, double* resid, int outputs_on_device,
+                          rafeast_info* info) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !m_found || !evals) return RAFEAST_ERR_INVALID_ARG;
+  if (world < 1 || rank < 0 || rank >= world || (world > 1 && !sum))
+    return RAFEAST_ERR_INVALID_ARG;
+  if (mode != RAFEAST_SHARD_COLUMNS && mode != RAFEAST_SHARD_SHIFTS) return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  validate_params(prm);
+  RF_CHECK(prm->reserved == 0, RAFEAST_ERR_INVALID_ARG);
+  RF_CHECK(prm->m0 <= h->n, RAFEAST_ERR_INVALID_ARG);
+  CallScope scope(h);
+  SolveRun r;
+  solve_begin(r, h, *prm);
+  int lo = 0, hi = 0;
+  rafeast_shard_range(mode, r.m0, prm->nc, rank, world, &lo, &hi);
+  // the shift range lives in the handle for the filter's duration only
+  struct ShardGuard {
+    Handle* h;
+    ~ShardGuard() {
+      h->shard_j0 = 0;
+      h->shard_j1 = -1;
+    }
+  } guard{h};
+  double* flag = (double*)scratch(h, S_SHARD, 64);
+  const size_t qt_bytes = sizeof(double) * h->n * r.ldq;
+  auto exchange = [&](double* buf, int64_t count) {
+    RF_CUDA(cudaStreamSynchronize(h->stream));
+    if (sum(ctx, buf, count) != 0) {
+      snprintf(g_err, sizeof(g_err), "sum callback failed (rank %d of %d)", rank, world);
+      throw Err{RAFEAST_ERR_EXCHANGE};
+    }
+  };
+  for (r.it = 1; r.it <= prm->max_outer; ++r.it) {
+    RF_CUDA(cudaEventRecord(r.ev[2], h->stream));
+    // this rank's share of Q~; the other ranks' columns (or nodes) stay zero,
+    // so that the sum over ranks is the whole filtered block
+    if (world > 1) RF_CUDA(cudaMemsetAsync(r.Qt, 0, qt_bytes, h->stream));
+    r.fs = FilterStats();
+    if (hi > lo) {
+      if (mode == RAFEAST_SHARD_COLUMNS) {
+        const std::vector<double> th(h->theta.begin() + lo, h->theta.begin() + hi);
+        run_filter(h, *prm, h->Q + lo, h->AQ + lo, h->theta_d + lo, th, hi - lo, r.ldq,
+                   r.Qt + lo, r.fs);
+      } else {
+        h->shard_j0 = lo;
+        h->shard_j1 = hi;
+        run_filter(h, *prm, h->Q, h->AQ, h->theta_d, h->theta, r.m0, r.ldq, r.Qt, r.fs);
+        h->shard_j0 = 0;
+        h->shard_j1 = -1;
+      }
+    }
+    if (world > 1) exchange(r.Qt, (int64_t)h->n * r.ldq);
+    r.cocg_total += r.fs.iters_max;
+    RF_CUDA(cudaEventRecord(r.ev[3], h->stream));
+    bool done = solve_outer_tail(r);
+    if (world > 1) {
+      // every rank runs the same dense steps on the same block; the ranks
+      // still agree on stopping (all converged), so that no rank leaves the
+      // loop while another waits in the next sum
+      const double one = done ? 1.0 : 0.0;
+      RF_CUDA(cudaMemcpyAsync(flag, &one, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      exchange(flag, 1);
+      double tot = 0.0;
+      RF_CUDA(cudaMemcpyAsync(&tot, flag, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      RF_CUDA(cudaStreamSynchronize(h->stream));
+      done = tot > world - 0.5;
+      if (!done) r.status = RAFEAST_NO_CONVERGENCE;
+    }
+    if (done) break;
   }
   if (r.it > prm->max_outer) r.it = prm->max_outer;
   const int status = solve_finish(r, m_found, evals, evecs, resid, outputs_on_device, info);

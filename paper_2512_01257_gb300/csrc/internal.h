@@ -248,6 +248,9 @@ struct Handle {
   int opt_tile_cb = 0;      // tiled dot kernel: forced column pairs per block (0: autotuned)
   int opt_dense = 0;        // FP64 Gram matrices: 0 tensor cores (digit split), 1 FP64 pipe
   int opt_defer = 0;        // 1: deferred shifted updates with the tiled dot kernel, 0: never
+  // quadrature nodes [shard_j0, shard_j1) of the N_c this filter sums over
+  // (a shift-sharded solve); shard_j1 < 0: all of them
+  int shard_j0 = 0, shard_j1 = -1;
   // autotuned kernel shapes (lanes, chunks per lane) of the multi-shift
   // kernels, keyed by (pairs, shifts, precision)
   struct Shape {
@@ -280,7 +283,7 @@ void* scratch(Handle* h, int slot, size_t bytes);  // keep-alive buffer per slot
 void ensure_dyn_smem(const void* fn, size_t bytes);
 enum Slot {
   S_STATE = 0, S_DACC, S_QT, S_TMP1, S_TMP2, S_SCAL, S_GRAM, S_SMALL, S_OMEGA,
-  S_AQ2, S_IO1, S_IO2, S_BATCH, S_TPART, S_COUNT
+  S_AQ2, S_IO1, S_IO2, S_BATCH, S_TPART, S_SHARD, S_COUNT
 };
 
 // ---- host math (hostmath.cpp) ------------------------------------------------

@@ -30,6 +30,7 @@ RAFEAST_ERR_OUT_OF_MEMORY = -6
 RAFEAST_ERR_NOT_READY = -7
 RAFEAST_ERR_CHOLESKY = -8
 RAFEAST_ERR_NO_DEVICE = -9
+RAFEAST_ERR_EXCHANGE = -10
 
 RAFEAST_FP64 = 0
 RAFEAST_MIXED = 1
@@ -37,6 +38,8 @@ RAFEAST_FORM_DIRECT = 0
 RAFEAST_FORM_CORRECTION = 1
 RAFEAST_START_RANDOM = 0
 RAFEAST_START_SUBSPACE = 1
+RAFEAST_SHARD_COLUMNS = 0
+RAFEAST_SHARD_SHIFTS = 1
 RAFEAST_CREATE_NO_REORDER = 1
 RAFEAST_CREATE_FORCE_REORDER = 2
 RAFEAST_CREATE_CHECK_SYMMETRY = 4
@@ -66,8 +69,12 @@ EXPORTS = [
     "rafeast_rayleigh_ritz", "rafeast_warmstart", "rafeast_set_subspace",
     "rafeast_get_subspace", "rafeast_solve", "rafeast_solve_batched", "rafeast_profile",
     "rafeast_last_error", "rafeast_profile_history", "rafeast_gram",
-    "rafeast_gram_noalloc",
+    "rafeast_gram_noalloc", "rafeast_shard_range", "rafeast_partition_instances",
+    "rafeast_solve_sharded",
 ]
+
+# int (*rafeast_sum_fn)(void* ctx, double* buf, int64_t count)
+SUM_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int64)
 
 
 class RafeastParams(C.Structure):
@@ -137,6 +144,10 @@ def load():
                               C.POINTER(RafeastInfo)]),
         "rafeast_solve_batched": (I, [I, P, C.POINTER(RafeastParams), P, P, P, P, I,
                                       C.POINTER(RafeastInfo), P]),
+        "rafeast_shard_range": (I, [I, I, I, I, I, C.POINTER(I), C.POINTER(I)]),
+        "rafeast_partition_instances": (I, [I, P, I, P]),
+        "rafeast_solve_sharded": (I, [P, C.POINTER(RafeastParams), I, I, I, SUM_FN, P,
+                                      C.POINTER(I), P, P, P, I, C.POINTER(RafeastInfo)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -372,3 +383,77 @@ def rafeast_solve_batched(handles, params, evals, evecs=None, resid=None):
     rc = load().rafeast_solve_batched(n, H, Pa, MF, E, V, R, dev, INF, ST)
     _check(rc, "rafeast_solve_batched")
     return list(ST), list(MF), list(INF)
+
+
+def rafeast_shard_range(mode, m0, nc, rank, world):
+    """(lo, hi): the columns (RAFEAST_SHARD_COLUMNS) or quadrature nodes
+    (RAFEAST_SHARD_SHIFTS) that rank filters in a sharded solve."""
+    lo, hi = C.c_int(), C.c_int()
+    _check(load().rafeast_shard_range(int(mode), int(m0), int(nc), int(rank), int(world),
+                                      C.byref(lo), C.byref(hi)), "rafeast_shard_range")
+    return lo.value, hi.value
+
+
+def rafeast_partition_instances(costs, world):
+    """owner[i]: the rank that solves problem i (longest first, least loaded)."""
+    cost = np.ascontiguousarray(costs, dtype=np.int64)
+    owner = np.zeros(len(cost), dtype=np.int32)
+    _check(load().rafeast_partition_instances(len(cost), _ptr(cost), int(world), _ptr(owner)),
+           "rafeast_partition_instances")
+    return owner
+
+
+class _DeviceView:
+    """A (count,) float64 view of device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, count):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": "<f8",
+                                         "data": (int(ptr), False), "strides": None,
+                                         "version": 2}
+
+
+def device_tensor(ptr, count):
+    """torch float64 tensor over count doubles of device memory at ptr (no copy)."""
+    import torch
+    return torch.as_tensor(_DeviceView(ptr, count), device="cuda")
+
+
+def allreduce_sum(group=None):
+    """Sum over the ranks of a torch.distributed group (NCCL, or gloo with
+    CUDA tensors) for rafeast_solve_sharded: an all-reduce of the block in
+    place, finished before the call returns."""
+    import torch
+    import torch.distributed as dist
+
+    def fn(t):
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        if t.is_cuda:
+            torch.cuda.current_stream(t.device).synchronize()
+    return fn
+
+
+def rafeast_solve_sharded(h, params, mode, rank, world, sum_fn, evals, evecs=None, resid=None):
+    """rafeast_solve on rank `rank` of `world`. sum_fn(t) receives a torch
+    float64 CUDA tensor viewing the library's block and must leave in it the
+    sum over ranks (e.g. allreduce_sum()). An exception in sum_fn fails the
+    solve and is raised here. Returns (status, m_found, info)."""
+    info = RafeastInfo()
+    mf = C.c_int()
+    dev = _on_device(evals)
+    failure = []
+
+    def cb(_ctx, buf, count):
+        try:
+            sum_fn(device_tensor(buf, count))
+            return 0
+        except BaseException as e:  # noqa: BLE001 (reported after the call)
+            failure.append(e)
+            return 1
+    fn = SUM_FN(cb) if sum_fn is not None else SUM_FN()
+    rc = load().rafeast_solve_sharded(h, C.byref(params), int(mode), int(rank), int(world), fn,
+                                      None, C.byref(mf), _ptr(evals), _ptr(evecs), _ptr(resid),
+                                      dev, C.byref(info))
+    if failure:
+        raise RafeastError(rc, "rafeast_solve_sharded: sum callback") from failure[0]
+    _check(rc, "rafeast_solve_sharded", ok=(0, 1, 2, 3))
+    return rc, mf.value, info

@@ -1,13 +1,14 @@
-"""The N > 1 path of bench.py on CPU: one replica per rank (the path has no
-exchange step), max-over-ranks timing and the whole-job rate, on a
-world-size-2 gloo process group; the reference arm's rank 1 exits without
-work or output."""
+"""The N > 1 path of bench.py on CPU: max-over-ranks timing, the whole-job
+rate of replicas and of sharded runs, the instance shares of the batched
+workload, on a world-size-2 gloo process group where ranks are involved; the
+reference arm's rank 1 exits without work or output."""
 import json
 import os
 import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -60,3 +61,21 @@ def test_reference_arm_other_ranks_exit_quietly():
                        capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_sharded_rate_and_instance_shares():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2512_01257_gb300 import build, rafeast as R
+    if not os.path.exists(R.LIB_PATH):
+        build.build()
+    # one solve shared by the ranks in 250 ms: 4 solves/s whatever the N
+    assert bench.sharded_rate(1, 250.0) == pytest.approx(4.0)
+    costs = [int(c) for c in (np.random.default_rng(3).integers(1, 10**6, 64))]
+    assert bench.my_instances(costs, 1, 0) == list(range(64))
+    for world in (2, 3, 8):
+        shares = [bench.my_instances(costs, world, r, R) for r in range(world)]
+        # every problem solved once, by one rank
+        assert sorted(t for s in shares for t in s) == list(range(64))
+        loads = [sum(costs[t] for t in s) for s in shares]
+        assert max(loads) <= sum(costs) / world + max(costs)
