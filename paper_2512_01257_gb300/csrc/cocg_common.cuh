@@ -319,6 +319,207 @@ __device__ void ms_scalar_cols(const CocgArgs<T>& a, int k, int c0, int c1, MsCo
   *worst_out = worst;
 }
 
+// the seed system's results of one column, handed from phase A to phases B
+// and C of ms_scalar_cols_wide (shared memory)
+struct MsSeed {
+  SysState st;
+  double gre, gim, are, aim, bre, bim, nu, thr;
+  int on, seed_ok, seed_running, any;
+};
+
+// ms_scalar_cols for a whole CTA: the same arithmetic, value for value, in
+// three phases so that the shifted systems of a column are computed side by
+// side instead of one after another: (A) a thread per column takes the seed
+// system (its sums from sacc[5 (i - c0) ..] in shared memory); (B) a thread
+// per (column, shifted system) takes that system; (C) a thread per column
+// writes the column's state and coefficients. sd: shared memory for c1 - c0
+// MsSeed records. Every thread of the CTA calls it.
+template <typename T>
+__device__ void ms_scalar_cols_wide(const CocgArgs<T>& a, int k, int c0, int c1,
+                                    const double* sacc, MsSeed* sd, MsCount& cnt,
+                                    double* worst_out) {
+  using Seed = MsSeed;
+  const int ns = a.ns, nci = c1 - c0;
+  double worst = 0.0;
+  // (A) the seed system
+  for (int ii = threadIdx.x; ii < nci; ii += blockDim.x) {
+    const int i = c0 + ii;
+    Seed s;
+    s.st = a.st[i];
+    s.gre = sacc[5 * ii + 0];
+    s.gim = sacc[5 * ii + 1];
+    const double dre = sacc[5 * ii + 2], dim = sacc[5 * ii + 3];
+    s.nu = sacc[5 * ii + 4];
+    s.on = s.st.active != 0;
+    s.any = 0;
+    s.are = s.aim = s.bre = s.bim = s.thr = 0.0;
+    s.seed_ok = 0;
+    s.seed_running = 0;
+    if (s.on) {
+      SysState& st = s.st;
+      const double gre = s.gre, gim = s.gim, nu = s.nu;
+      if (k == 0) st.bnorm2 = nu;
+      if (st.bnorm2 > 0.0) worst = fmax(worst, nu / st.bnorm2);
+      double bre = 0.0, bim = 0.0, mre = dre, mim = dim;
+      if (k > 0) {
+        const double2 gp = st.gamma_prev;
+        const double den = gp.x * gp.x + gp.y * gp.y;
+        bre = (gre * gp.x + gim * gp.y) / den;
+        bim = (gim * gp.x - gre * gp.y) / den;
+        const double2 ap = st.alpha_prev;
+        const double da = ap.x * ap.x + ap.y * ap.y;
+        const double bgr = bre * gre - bim * gim, bgi = bre * gim + bim * gre;
+        mre = dre - (bgr * ap.x + bgi * ap.y) / da;
+        mim = dim - (bgi * ap.x - bgr * ap.y) / da;
+      }
+      const double mm = mre * mre + mim * mim;
+      const bool seed_ok = mm > 1e-300 && isfinite(mm) && isfinite(bre) && isfinite(bim);
+      s.are = seed_ok ? (gre * mre + gim * mim) / mm : 0.0;
+      s.aim = seed_ok ? (gim * mre - gre * mim) / mm : 0.0;
+      s.bre = bre;
+      s.bim = bim;
+      s.seed_ok = seed_ok;
+      s.thr = a.tol2 * st.bnorm2;
+      bool seed_running = st.iters < 0 || k == 0;
+      if (seed_running && (nu <= s.thr || k >= a.max_inner || !seed_ok)) {
+        if (!(nu <= s.thr)) {
+          if (!seed_ok) atomicAdd(&cnt.brk, 1);
+          else atomicAdd(&cnt.cap, 1);
+        }
+        st.iters = k;
+        seed_running = false;
+        if (st.bnorm2 > 0.0) {
+          atomicMax(&cnt.mx, k);
+          atomicMin(&cnt.mn, k);
+        }
+      } else if (seed_running) {
+        st.iters = -1;
+        s.any = 1;
+      }
+      s.seed_running = seed_running;
+    }
+    sd[ii] = s;
+  }
+  __syncthreads();
+  // (B) the shifted systems
+  for (int e = threadIdx.x; e < nci * ns; e += blockDim.x) {
+    const int ii = e / ns, t = e - (e / ns) * ns, i = c0 + ii;
+    const Seed& s = sd[ii];
+    if (!s.on) continue;
+    const double nu = s.nu, thr = s.thr, are = s.are, aim = s.aim, bre = s.bre, bim = s.bim;
+    const bool seed_ok = s.seed_ok != 0;
+    ShiftState ss = a.sst[i * ns + t];
+    ShiftCoef<T> sc;
+    sc.pad = (T)0;
+    sc.act = (T)0;
+    sc.zeta = mk<T>((T)0, (T)0);
+    sc.beta = mk<T>((T)1, (T)0);
+    sc.ca = mk<T>((T)0, (T)0);
+    if (ss.active) {
+      const double zr = ss.zeta.x, zi = ss.zeta.y;
+      const double nuj = (zr * zr + zi * zi) * nu;
+      if (nuj <= thr || k >= a.max_inner || !seed_ok) {
+        if (!(nuj <= thr)) {
+          if (!seed_ok) atomicAdd(&cnt.brk, 1);
+          else atomicAdd(&cnt.cap, 1);
+        }
+        ss.active = 0;
+        ss.iters = k;
+        if (s.st.bnorm2 > 0.0) {
+          atomicMax(&cnt.mx, k);
+          atomicMin(&cnt.mn, k);
+        }
+      } else {
+        const double2 sg = a.sigma[t];
+        const double2 ap = k == 0 ? make_double2(1.0, 0.0) : s.st.alpha_prev;
+        const double2 zp = ss.zeta_prev, zc = ss.zeta;
+        double nre = zc.x * zp.x - zc.y * zp.y, nim = zc.x * zp.y + zc.y * zp.x;
+        const double tr = nre * ap.x - nim * ap.y, ti = nre * ap.y + nim * ap.x;
+        nre = tr;
+        nim = ti;
+        const double s1r = 1.0 + sg.x * are - sg.y * aim, s1i = sg.x * aim + sg.y * are;
+        double d1r = zp.x * ap.x - zp.y * ap.y, d1i = zp.x * ap.y + zp.y * ap.x;
+        const double t1r = d1r * s1r - d1i * s1i, t1i = d1r * s1i + d1i * s1r;
+        const double abr = are * bre - aim * bim, abi = are * bim + aim * bre;
+        const double dzr = zp.x - zc.x, dzi = zp.y - zc.y;
+        const double t2r = abr * dzr - abi * dzi, t2i = abr * dzi + abi * dzr;
+        const double der = t1r + t2r, dei = t1i + t2i;
+        const double dd = der * der + dei * dei;
+        const double znr = (nre * der + nim * dei) / dd, zni = (nim * der - nre * dei) / dd;
+        const double zc2 = zc.x * zc.x + zc.y * zc.y;
+        const double zp2 = zp.x * zp.x + zp.y * zp.y;
+        if (!(dd > 1e-300) || !isfinite(znr) || !isfinite(zni) || !(zc2 > 1e-300) ||
+            !(zp2 > 1e-300)) {
+          ss.active = 0;
+          ss.iters = k;
+          atomicAdd(&cnt.brk, 1);
+        } else {
+          const double qr = (znr * zc.x + zni * zc.y) / zc2, qi = (zni * zc.x - znr * zc.y) / zc2;
+          const double ajr = are * qr - aim * qi, aji = are * qi + aim * qr;
+          const double rr = (zc.x * zp.x + zc.y * zp.y) / zp2, ri = (zc.y * zp.x - zc.x * zp.y) / zp2;
+          const double r2r = rr * rr - ri * ri, r2i = 2.0 * rr * ri;
+          const double bjr = bre * r2r - bim * r2i, bji = bre * r2i + bim * r2r;
+          const double2 cq = a.scoef[i * ns + t];
+          sc.act = (T)1;
+          sc.zeta = mk<T>((T)zc.x, (T)zc.y);
+          sc.beta = mk<T>((T)bjr, (T)bji);
+          sc.ca = mk<T>((T)(cq.x * ajr - cq.y * aji), (T)(cq.x * aji + cq.y * ajr));
+          ss.zeta_prev = zc;
+          ss.zeta = make_double2(znr, zni);
+          atomicOr(&sd[ii].any, 1);
+        }
+      }
+    }
+    a.sst[i * ns + t] = ss;
+    a.scf[i * ns + t] = sc;
+  }
+  __syncthreads();
+  // (C) the column's state and coefficients
+  for (int ii = threadIdx.x; ii < nci; ii += blockDim.x) {
+    const int i = c0 + ii;
+    const Seed& s = sd[ii];
+    SysState st = s.st;
+    Coef<T> cf;
+    cf.pad = (T)0;
+    bool column_on = s.on != 0;
+    if (column_on) {
+      if (s.any) {
+        st.gamma_prev = make_double2(s.gre, s.gim);
+        st.alpha_prev = make_double2(s.are, s.aim);
+        const double2 cq = a.coef[i];
+        cf.ar = (T)1;
+        cf.beta = mk<T>((T)s.bre, (T)s.bim);
+        cf.alpha = mk<T>((T)s.are, (T)s.aim);
+        cf.ca = s.seed_running
+                    ? mk<T>((T)(cq.x * s.are - cq.y * s.aim), (T)(cq.x * s.aim + cq.y * s.are))
+                    : mk<T>((T)0, (T)0);
+        atomicAdd(&cnt.active, 1);
+      } else {
+        st.active = 0;
+        column_on = false;
+      }
+    }
+    if (!column_on) {
+      cf.ar = (T)0;
+      cf.beta = mk<T>((T)1, (T)0);
+      cf.alpha = mk<T>((T)0, (T)0);
+      cf.ca = mk<T>((T)0, (T)0);
+      for (int t = 0; t < ns; ++t) {
+        ShiftCoef<T> sc;
+        sc.pad = (T)0;
+        sc.act = (T)0;
+        sc.zeta = mk<T>((T)0, (T)0);
+        sc.beta = mk<T>((T)1, (T)0);
+        sc.ca = mk<T>((T)0, (T)0);
+        a.scf[i * ns + t] = sc;
+      }
+    }
+    a.st[i] = st;
+    a.cf[i] = cf;
+  }
+  *worst_out = worst;
+}
+
 // column activity of the pairs [p0, p1) after their columns' step; counts
 // the active pairs into cnt.cols
 template <typename T>

@@ -34,6 +34,7 @@
 // The gathered sums are accumulated entry by entry in CSR order, exactly as
 // the register-gather kernel (cocg_kernels.cuh) does, so w is the same to the
 // last bit in both.
+#include <algorithm>
 #include <cstddef>
 
 #include "cocg_kernels.cuh"
@@ -187,25 +188,57 @@ __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a
   }
   const float* __restrict__ Rprev = a.r[buf ^ 1];  // r_{k-1}
   const int nitems = tl.ntiles * ncb;
+  // the index data of the next item is loaded into registers while this
+  // item's rows gather (this thread's share: union rows u = tid + TT c, row
+  // pointers r = tid + TT c), and stored into tb once the gathers are done
+  constexpr int UPT = (TILE_UCAP + TT - 1) / TT, RPT = (TILE_TMAX + 1 + TT - 1) / TT;
+  int f_r0 = 0, f_nr = 0, f_nu = 0, f_us = 0;
+  int f_sidx[UPT], f_srp[RPT];
+  auto fetch = [&](int it) {
+    const int t = it / ncb;
+    f_r0 = __ldg(tl.trow + t);
+    f_nr = __ldg(tl.trow + t + 1) - f_r0;
+    const int u0 = __ldg(tl.uoff + t);
+    f_nu = __ldg(tl.uoff + t + 1) - u0;
+    f_us = __ldg(tl.uself + t);
+#pragma unroll
+    for (int c = 0; c < UPT; ++c) {
+      const int u = threadIdx.x + TT * c;
+      f_sidx[c] = u < f_nu ? __ldg(tl.ucol + u0 + u) : 0;
+    }
+#pragma unroll
+    for (int c = 0; c < RPT; ++c) {
+      const int r = threadIdx.x + TT * c;
+      f_srp[c] = r <= f_nr ? __ldg(rowptr + f_r0 + r) : 0;
+    }
+  };
+  if (any && (int)blockIdx.x < nitems) fetch(blockIdx.x);
   for (int item = blockIdx.x; any && item < nitems; item += gridDim.x) {
-    // the tile's indices (plain loads, all in flight together), then the
+    // the tile's indices (fetched during the last item's gathers), then the
     // copies, which no longer wait on a global load each
-    const int t = item / ncb;
-    const int r0 = __ldg(tl.trow + t), nr = __ldg(tl.trow + t + 1) - r0;
-    const int u0 = __ldg(tl.uoff + t), nu = __ldg(tl.uoff + t + 1) - u0;
-    for (int u = threadIdx.x; u < nu; u += TT) tb.sidx[u] = __ldg(tl.ucol + u0 + u);
-    for (int r = threadIdx.x; r <= nr; r += TT) tb.srp[r] = __ldg(rowptr + r0 + r);
+    const int r0 = f_r0, nr = f_nr, nu = f_nu;
+#pragma unroll
+    for (int c = 0; c < UPT; ++c) {
+      const int u = threadIdx.x + TT * c;
+      if (u < nu) tb.sidx[u] = f_sidx[c];
+    }
+#pragma unroll
+    for (int c = 0; c < RPT; ++c) {
+      const int r = threadIdx.x + TT * c;
+      if (r <= nr) tb.srp[r] = f_srp[c];
+    }
     if (threadIdx.x == 0) {
       tb.r0 = r0;
       tb.nr = nr;
       tb.nu = nu;
-      tb.us = __ldg(tl.uself + t);
-      tb.kbase = __ldg(rowptr + r0) & ~7;
+      tb.us = f_us;
+      tb.kbase = f_srp[0] & ~7;
     }
     __syncthreads();
     tile_copies<CB>(tl, tb, xs, R, ldt, cbk, sact);
     cp_async_wait_all();
     __syncthreads();
+    if (item + (int)gridDim.x < nitems) fetch(item + gridDim.x);
     const uint16_t* slx = tb.slx;
     const int kbase = tb.kbase, us = tb.us;
     if (on) {
@@ -296,8 +329,10 @@ __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a
     double s = 0.0;
     for (int r = 0; r < NRS; ++r) s += sred[(r * CB + jj) * 10 + t];
     tl.part[((int64_t)blockIdx.x * CB + jj) * 10 + t] = s;
+    // (only the writers of part fence before the ticket: the other threads'
+    // stores of w need not be waited for here)
+    __threadfence();
   }
-  __threadfence();
   __syncthreads();
   // the last CTA of this column block adds the block's CTA sums and runs
   // the scalar step of the block's columns; the last column block to finish
@@ -308,6 +343,10 @@ __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  // the block's sums, per column: gamma (re, im), delta (re, im), nu, and the
+  // seed records of the scalar step, in the (now free) staging area
+  double* s_acc = reinterpret_cast<double*>(xs);
+  MsSeed* s_seed = reinterpret_cast<MsSeed*>(s_acc + 2 * CB * 5);
   {
     // value v = (pair jj, sum t): lane l adds the CTAs l, l + 32, ... of the
     // block in that order, then the warp adds its lanes by a fixed tree
@@ -319,19 +358,16 @@ __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a
         sv += __ldcg(tl.part + ((int64_t)(cbk + b * ncb) * CB + jj) * 10 + t);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-      const int qq = cbk * CB + jj;
-      if (lane == 0 && qq < a.m0) a.acc[5 * (2 * qq + t / 5) + t % 5] = sv;
+      if (lane == 0) s_acc[5 * (2 * jj + t / 5) + t % 5] = sv;
     }
   }
-  __threadfence();
-  __syncthreads();
   __shared__ MsCount cnt;
   if (threadIdx.x == 0) ms_count_init(cnt);
   __syncthreads();
   const int k = __ldcg(&a.ctl->iter);
   const int p0 = cbk * CB, p1 = min(a.m0, p0 + CB);
   double worst = 0.0;
-  ms_scalar_cols<float>(a, k, 2 * p0, 2 * p1, cnt, &worst);
+  ms_scalar_cols_wide<float>(a, k, 2 * p0, 2 * p1, s_acc, s_seed, cnt, &worst);
   __syncthreads();
   ms_colact<float>(a, p0, p1, cnt);
   __syncthreads();
@@ -373,7 +409,8 @@ static void launch_cb(const CocgArgs<float>& a, const TileArgs& tl, int buf, int
                       int occ_cap, cudaStream_t s) {
   auto kern = k_ms_dots_tiled<CB, VF>;
   const size_t stage = (size_t)tl.max_union * CB * sizeof(float4);
-  const size_t red = (size_t)TT * 10 * sizeof(double);
+  const size_t red = std::max((size_t)TT * 10 * sizeof(double),
+                              2 * CB * 5 * sizeof(double) + 2 * CB * sizeof(MsSeed));
   const size_t coef = a.defer ? (size_t)CB * 2 * a.ns * sizeof(DefCoef) : 0;
   const size_t smem = (stage > red ? stage : red) + coef;
   ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
