@@ -446,9 +446,11 @@ def run_batched(args):
         l1 = torch.cuda.Event(enable_timing=True)
         l0.record(stream)
         warm(hs)
+        loop_info = []
         for t in range(cnt):
-            st, _, _ = R.rafeast_solve(hs[t], prms[t], evals[t], evecs[t], resid[t])
+            st, _, inf = R.rafeast_solve(hs[t], prms[t], evals[t], evecs[t], resid[t])
             assert st in (R.RAFEAST_OK, R.RAFEAST_NO_CONVERGENCE)
+            loop_info.append(inf)
         l1.record(stream)
         torch.cuda.synchronize()
         loop_ms = l0.elapsed_time(l1)
@@ -457,7 +459,15 @@ def run_batched(args):
             R.rafeast_set_option(h, R.RAFEAST_OPT_PROFILE, 0)
         loop_kernels = {"dots_ms": sum(p["dots_ms"] for p in lp),
                         "update_ms": sum(p["update_ms"] for p in lp),
-                        "steps": int(sum(p["dots_launches"] for p in lp))}
+                        "steps": int(sum(p["dots_launches"] for p in lp)),
+                        # the slowest problems solved alone: the batched
+                        # step cannot end before the slowest of them
+                        "slowest": [{"n": laps[t].n, "outer": loop_info[t].outer_iters,
+                                     "ms": loop_info[t].t_total_ms,
+                                     "filter_ms": loop_info[t].t_filter_ms,
+                                     "orth_ms": loop_info[t].t_orth_ms,
+                                     "rr_ms": loop_info[t].t_rr_ms}
+                                    for t in sorted(range(cnt), key=lambda t: -loop_info[t].t_total_ms)[:4]]}
     peak, peak_kind = _peaks()
     pre = "update" if prof["update_ms"] >= prof["dots_ms"] else "dots"
     names = {"update": "ms_update_grouped", "dots": "ms_dots_grouped"}
@@ -503,6 +513,12 @@ def run_batched(args):
                        "all_found": found_all, "gate": 1e-8,
                        "converged": n_conv, "count": total},
             "outer_iters_max": it_max,
+            # per-problem phase times of the last step, summed over this
+            # rank's problems (they overlap on the problems' own streams)
+            "phases_ms_sum": {"filter_ms": sum(i.t_filter_ms for i in infos),
+                              "orth_ms": sum(i.t_orth_ms for i in infos),
+                              "rr_ms": sum(i.t_rr_ms for i in infos),
+                              "total_ms_max": max(i.t_total_ms for i in infos)},
             "outer_iters_mean": it_sum / total,
             "per_instance_loop_ms": loop_ms, "per_instance_loop_kernels": loop_kernels,
             "batched_kernels": {"dots_ms": prof["dots_ms"] / args.steps,

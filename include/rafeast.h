@@ -320,6 +320,15 @@ int rafeast_orthonormalize(rafeast_t h, int m, double* Q, double* R);
  * Per-CTA partial sums live in the handle's scratch. m in 1..128. */
 int rafeast_gram(rafeast_t h, int m, const double* X, const double* Y, double* G);
 
+/* Tall block product Y = X M (the products X R^{-1} of Cholesky-QR and
+ * Q V of Rayleigh-Ritz in Algorithm 1 are of this form). X: device, n x m
+ * column-major (n of the handle); M: device, m x mo column-major; Y: device,
+ * n x mo column-major, entry (i, b) = sum_a X(i, a) M(a, b), FP64 accurate:
+ * on the tensor cores through exact BF16 digits of the FP64 values unless
+ * RAFEAST_OPT_DENSE = 1. m, mo in 1..128. */
+int rafeast_block_product(rafeast_t h, int m, const double* X, const double* M, int mo,
+                          double* Y);
+
 /* Allocation-free Gram matrix (no counterpart in the paper; a service for
  * callers): the same G = X^T Y as rafeast_gram, without a handle and without
  * any device allocation during the call. Some callers cannot let a library

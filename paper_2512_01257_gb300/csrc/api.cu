@@ -154,6 +154,22 @@ static void gram_dev(Handle* h, const double* X, const double* Y, int m, int ld,
     gram(X, Y, h->n, m, ld, G, d.part, h->num_sms, h->stream, sym, f32);
 }
 
+// Y = X M (tall n x m block times m x mo, row-major M) on the tensor cores
+// (exact BF16 digits of the FP64 values, kernels_tc.cu) unless the FP64 pipe
+// is asked for; upper: M is upper triangular (the FP64 kernel skips its zero
+// blocks)
+static void tall_dev(Handle* h, const double* X, int m, int ldx, const double* M, int mo,
+                     double* Y, int ldy, bool upper = false) {
+  if (h->opt_dense == 0 && tall_tc_fits(m, mo)) {
+    // (the timeout flag beside the dense status words; no other scratch is
+    // touched, so the caller's dense workspace stays where it is)
+    int* err = (int*)scratch(h, S_SMALL, 64) + 3;
+    tall_gemm_tc(X, h->n, m, ldx, M, mo, Y, ldy, h->num_sms, err, h->stream);
+  } else {
+    tall_gemm(X, h->n, m, ldx, M, mo, Y, ldy, h->stream, upper);
+  }
+}
+
 // X (n x m, ld) <- X R^{-1}; returns number of shifted passes; R_total (host,
 // m x m row-major upper) accumulates the factor if non-null. low_first: the
 // first pass forms its Gram in float, as in cholqr_rr below (the pass only
@@ -192,7 +208,7 @@ static int cholqr(Handle* h, double*& X, double*& tmp, int m, int ld, std::vecto
       ++shifted;
       if (passes < 4) ++passes;
     }
-    tall_gemm(X, h->n, m, ld, d.Rinv, m, tmp, ld, h->stream, true);
+    tall_dev(h, X, m, ld, d.Rinv, m, tmp, ld, true);
     h->launches += 1;
     std::swap(X, tmp);
     if (Rtot) {
@@ -223,7 +239,7 @@ static void rayleigh_ritz_dev(Handle* h, const double* X, int m, int ld, double*
                            h->num_sms, h->stream);
   gram_dev(h, X, tmp, m, ld, d.G, d, true);
   jacobi_eigh(d.G, m, theta_d, d.V, d.Vw, h->stream);
-  tall_gemm(X, h->n, m, ld, d.V, m, Qout, ld, h->stream);
+  tall_dev(h, X, m, ld, d.V, m, Qout, ld);
   // A Q by the (memory-bound) SpMM rather than (A X) V by an FP64 GEMM
   launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m, ld, 1.0, h->shift, Qout,
                            AQout, h->num_sms, h->stream);
@@ -275,7 +291,7 @@ static int cholqr_rr(Handle* h, double*& X, double*& tmp, double* tmp2, int m, i
       if (passes < 4) ++passes;
     }
     if (pass == passes - 1) break;  // the last factor is folded into Rayleigh-Ritz
-    tall_gemm(X, h->n, m, ld, d.Rinv, m, tmp, ld, h->stream, true);
+    tall_dev(h, X, m, ld, d.Rinv, m, tmp, ld, true);
     h->launches += 1;
     std::swap(X, tmp);
   }
@@ -287,7 +303,7 @@ static int cholqr_rr(Handle* h, double*& X, double*& tmp, double* tmp2, int m, i
   small_gemm(d.Rinv, 1, d.R, 0, d.G, m, 1.0, 0.0, h->stream);            // R^-T (.)
   jacobi_eigh(d.G, m, theta_d, d.V, d.Vw, h->stream);
   small_gemm(d.Rinv, 0, d.V, 0, d.R, m, 1.0, 0.0, h->stream);  // R^-1 V
-  tall_gemm(X, h->n, m, ld, d.R, m, Qout, ld, h->stream);
+  tall_dev(h, X, m, ld, d.R, m, Qout, ld);
   launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m, ld, 1.0, h->shift, Qout,
                            AQout, h->num_sms, h->stream);
   h->launches += 9;
@@ -2236,6 +2252,36 @@ int rafeast_gram(rafeast_t hh, int m, const double* X, const double* Y, double* 
   API_END
 }
 
+int rafeast_block_product(rafeast_t hh, int m, const double* X, const double* M, int mo,
+                          double* Y) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || m < 1 || m > 128 || mo < 1 || mo > 128 || !X || !M || !Y)
+    return RAFEAST_ERR_INVALID_ARG;
+  API_BEGIN
+  CallScope scope(h);
+  const int ldx = even(m), ldy = even(mo);
+  double* Xi = (double*)scratch(h, S_TMP1, sizeof(double) * h->n * ldx);
+  double* Yi = (double*)scratch(h, S_TMP2, sizeof(double) * h->n * ldy);
+  launch_to_internal(h->n, m, X, Xi, ldx, h->perm, h->stream);
+  // M: caller's column-major m x mo -> row-major, through the host (small)
+  std::vector<double> mc((size_t)m * mo), mr((size_t)m * mo);
+  RF_CUDA(cudaMemcpyAsync(mc.data(), M, sizeof(double) * m * mo, cudaMemcpyDeviceToHost,
+                          h->stream));
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < mo; ++b) mr[(size_t)a * mo + b] = mc[(size_t)b * m + a];
+  double* Mr = (double*)scratch(h, S_IO1, sizeof(double) * m * mo);
+  RF_CUDA(cudaMemcpyAsync(Mr, mr.data(), sizeof(double) * m * mo, cudaMemcpyHostToDevice,
+                          h->stream));
+  tall_dev(h, Xi, m, ldx, Mr, mo, Yi, ldy);
+  launch_from_internal(h->n, mo, Yi, ldy, Y, h->perm, nullptr, h->stream);
+  h->launches += 3;
+  scope.finish();
+  RF_CUDA(cudaStreamSynchronize(h->stream));
+  return RAFEAST_OK;
+  API_END
+}
+
 int rafeast_rayleigh_ritz(rafeast_t hh, int m, double* Q, double* theta, double* resid) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || m < 1 || m > 128 || !Q || !theta) return RAFEAST_ERR_INVALID_ARG;
@@ -2340,7 +2386,7 @@ int rafeast_warmstart(rafeast_t hh, double lmin, double lmax, int m0, int p, int
                           h->stream));
   RF_CUDA(cudaMemsetAsync(h->Q, 0, sizeof(double) * h->n * h->ldq, h->stream));
   RF_CUDA(cudaMemsetAsync(h->AQ, 0, sizeof(double) * h->n * h->ldq, h->stream));
-  tall_gemm(Y, h->n, k, ld, d.V, m0, h->Q, h->ldq, h->stream);
+  tall_dev(h, Y, k, ld, d.V, m0, h->Q, h->ldq);
   launch_spmm_real<double>(h->n, h->rowptr, h->colidx, h->val64, m0, h->ldq, 1.0, h->shift, h->Q,
                            h->AQ, h->num_sms, h->stream);
   h->launches += 2;

@@ -425,6 +425,11 @@ void gram_sum(const double* part, int parts, int m, bool sym, double* G, cudaStr
 // exact BF16 digits, tcgen05 products, exact integer accumulation; m <= 128,
 // partial: num_sms * m * m doubles; err (may be null) set on a timed-out wait
 bool gram_tc_fits(int m);
+// Y = X M on the tensor cores (exact BF16 digits of FP64 values, TMEM
+// levels): m, mo <= 128; err (device int) is set when a bounded wait ran out
+bool tall_tc_fits(int m, int mo);
+void tall_gemm_tc(const double* X, int64_t n, int m, int ldx, const double* M, int mo, double* Y,
+                  int ldy, int num_sms, int* err, cudaStream_t s);
 void gram_tc(const double* X, const double* Y, int64_t n, int m, int ld, double* G,
              double* partial, int num_sms, int* err, cudaStream_t s, bool sym);
 // Y = X * M (M: m x mo, ld mo); upper: M is upper triangular (m == mo)

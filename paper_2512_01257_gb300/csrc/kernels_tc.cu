@@ -43,6 +43,8 @@
 // to an mbarrier per buffer; every wait on it is bounded.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -384,7 +386,269 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
 }
 
+// ---------------------------------------------------------------------------
+// Tall product Y = X M (n x m times m x mo, m, mo <= 128) on the tensor cores,
+// the same exact digit arithmetic with the contraction over the m columns:
+//
+// 1. Scaling. A CTA owns a range of rows. Column a of X is scaled by 2^-c_a,
+//    c_a its largest exponent over those rows, and M's row a by 2^c_a (X M is
+//    unchanged, and a small column of X keeps its own relative precision).
+//    Row r of the scaled X is then written as integers F = round(x 2^(55-E_r))
+//    with E_r its largest exponent, and column b of the scaled M as integers
+//    G with its own exponent E_b; both are exact multiples of 2^-55 of their
+//    row's or column's largest value.
+// 2. Digits and levels as for the Gram: seven balanced base-256 digits per
+//    integer, here the 34 digit pairs with i + j <= 7 as tcgen05.mma (M = 128
+//    rows r, N = nb <= 64 columns b, K = 16 columns a) into eight FP32 levels
+//    of TMEM (8 x 64 columns). With K = m <= 128 a level adds at most
+//    7 x 128 products of at most 2^14: every level is an exact integer.
+// 3. y_rb = (I + L 2^-8) 2^(E_r + E_b - 38), I = sum_{l<=3} S_l 2^(8 (3-l))
+//    (an exact 64-bit integer) and L = S_4 + S_5 2^-8 + S_6 2^-16 + S_7 2^-24
+//    (exact in FP64): one rounding to FP64; the dropped pairs (i + j >= 8)
+//    change a product by less than 2^-61 of 2^(E_r + E_b), so the error is
+//    that of writing the values as integers, 2^-55 of the row's and of the
+//    column's largest scaled value per product.
+//
+// A row of X with a NaN or infinity gives a row of NaN, a column of M with
+// one a column of NaN. Operands are staged as in the Gram (K-major, 32-wide K
+// slices); the B digits of the CTA's columns are formed once, the A digits of
+// the next 32 columns of a 128-row block while the tensor cores multiply the
+// last ones.
+constexpr int TT_LEV = 8;     // levels kept (digit pairs with i + j <= 7)
+constexpr int TT_NAN_ROW = -1000000;
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_tall(const double* __restrict__ X, int64_t n, int m, int ldx,
+              const double* __restrict__ Mm, int mo, double* __restrict__ Y, int ldy, int nb,
+              int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  constexpr int ABUF = TC_DIG * TC_APLANE;  // one buffer of A digit planes (56 KB)
+  const int bpl = nb * 64;                  // bytes of one B digit plane of one K slice
+  unsigned char* Bp = tsm + 2 * ABUF;       // [slice][digit] planes
+  __shared__ int sCe[TC_M], sFb[TC_NB], sEr[TC_M], sEh[TC_M];
+  __shared__ uint32_t s_tbase;
+  __shared__ __align__(8) uint64_t s_mbar[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b0 = blockIdx.x * nb;
+  const int parts = gridDim.y;
+  const int64_t r_lo = n * (int64_t)blockIdx.y / parts;
+  const int64_t r_hi = n * (int64_t)(blockIdx.y + 1) / parts;
+  const int kp16 = (m + 15) & ~15, nsl = (kp16 + 31) / 32;
+  // (1) column exponents of X over this CTA's rows (finite values)
+  for (int t = tid; t < TC_M; t += TC_THREADS) sCe[t] = 0;
+  __syncthreads();
+  {
+    const int a = tid & (TC_M - 1);
+    int e = 0;
+    if (a < m)
+      for (int64_t r = r_lo + (tid >> 7); r < r_hi; r += 2) {
+        const int ex = (int)(((unsigned long long)__double_as_longlong(X[r * ldx + a]) >> 52) & 0x7FF);
+        if (ex != 0x7FF) e = max(e, ex);
+      }
+    atomicMax(&sCe[a], e);
+  }
+  __syncthreads();
+  // column exponents of the scaled M (0: the column is zero; -1: not finite)
+  if (tid < TC_NB) {
+    const int b = b0 + tid;
+    int f = 0;
+    bool bad = false;
+    if (tid < nb && b < mo)
+      for (int a = 0; a < m; ++a) {
+        const int ex = (int)(((unsigned long long)__double_as_longlong(Mm[(int64_t)a * mo + b]) >> 52) & 0x7FF);
+        if (ex == 0x7FF) bad = true;
+        else if (ex != 0 && sCe[a] != 0) f = max(f, ex + sCe[a]);
+      }
+    sFb[tid] = bad ? -1 : f;
+  }
+  __syncthreads();
+  // B digit planes of all K slices: scaled M^T (row b, K index a)
+  for (int e = tid; e < nb * (kp16 / 2); e += TC_THREADS) {
+    const int b = e % nb, ap = e / nb, a = 2 * ap;
+    const int fb = sFb[b];
+    long long F0 = 0, F1 = 0;
+    if (b0 + b < mo && fb > 0) {
+      if (a < m && sCe[a] != 0) F0 = tc_fixed(Mm[(int64_t)a * mo + b0 + b], fb - sCe[a]);
+      if (a + 1 < m && sCe[a + 1] != 0) F1 = tc_fixed(Mm[(int64_t)(a + 1) * mo + b0 + b], fb - sCe[a + 1]);
+    }
+    tc_store_pair(Bp + (a >> 5) * TC_DIG * bpl, bpl, tc_off(b, a & 31), F0, F1);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tbase)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = s_tbase;
+  const uint32_t idesc = tc_idesc(nb);
+  const int ra = 32 * (warp & 3) + lane, h = warp >> 2, nh = nb >> 1;
+  const uint32_t trow = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+  bool ok = true;
+  int g = 0;  // K slices issued so far (buffer g & 1, its commit's phase (g >> 1) & 1)
+  for (int64_t rb = r_lo; rb < r_hi && ok; rb += TC_M) {
+    // (2) row exponents of the scaled X: thread (r, half) scans the columns
+    // it will split, 16 of every 32, and the two halves are combined
+    {
+      const int r = tid & (TC_M - 1), half = tid >> 7;
+      const int64_t row = rb + r;
+      int e = -0x40000000;
+      bool bad = false;
+      if (row < r_hi)
+        for (int q = 0; q < nsl; ++q) {
+          const int a0 = 32 * q + 16 * half;
+#pragma unroll
+          for (int t = 0; t < 16; ++t)
+            if (a0 + t < m) {
+              const int ex =
+                  (int)(((unsigned long long)__double_as_longlong(X[row * ldx + a0 + t]) >> 52) & 0x7FF);
+              if (ex == 0x7FF) bad = true;
+              else if (ex != 0) e = max(e, ex - sCe[a0 + t]);
+            }
+        }
+      if (half) sEh[r] = bad ? TT_NAN_ROW : e;
+      __syncthreads();
+      if (!half) {
+        const int e1 = sEh[r];
+        sEr[r] = (bad || e1 == TT_NAN_ROW) ? TT_NAN_ROW : max(e, e1);
+      }
+    }
+    __syncthreads();
+    // (3) K slices: digits of the next 32 columns while the last ones multiply
+    for (int q = 0; q < nsl && ok; ++q, ++g) {
+      const int buf = g & 1;
+      unsigned char* A = tsm + buf * ABUF;
+      if (g >= 2) ok = __syncthreads_and(tc_wait(&s_mbar[buf], ((g - 2) >> 1) & 1));
+      if (!ok) break;
+      {
+        const int r = tid & (TC_M - 1), half = tid >> 7;
+        const int64_t row = rb + r;
+        const int er = sEr[r];
+        const bool on = row < r_hi && er != TT_NAN_ROW && er > -0x40000000;
+        const int a0 = 32 * q + 16 * half;
+        double xv[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) xv[t] = (on && a0 + t < m) ? X[row * ldx + a0 + t] : 0.0;
+#pragma unroll
+        for (int t = 0; t < 16; t += 2) {
+          const long long F0 = xv[t] != 0.0 ? tc_fixed(xv[t], sCe[a0 + t] + er) : 0;
+          const long long F1 = xv[t + 1] != 0.0 ? tc_fixed(xv[t + 1], sCe[a0 + t + 1] + er) : 0;
+          tc_store_pair(A, TC_APLANE, tc_off(r, 16 * half + t), F0, F1);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t ad0 = tc_desc(smem_u32(A));
+        const uint64_t bd0 = tc_desc(smem_u32(Bp + q * TC_DIG * bpl));
+        const int nks = min(2, (kp16 - 32 * q) / 16);
+        for (int ks = 0; ks < nks; ++ks) {
+#pragma unroll
+          for (int l = 0; l < TT_LEV; ++l) {
+            const int i0 = l > TC_DIG - 1 ? l - (TC_DIG - 1) : 0;
+#pragma unroll
+            for (int i = i0; i <= l && i < TC_DIG; ++i) {
+              const int j = l - i;
+              const uint64_t ad = ad0 + (uint64_t)((i * TC_APLANE + ks * 256) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((j * bpl + ks * 256) >> 4);
+              tc_mma(tbase + l * nb, ad, bd, idesc, (q == 0 && ks == 0 && i == i0) ? 0u : 1u);
+            }
+          }
+        }
+        tc_commit(&s_mbar[buf]);
+      }
+    }
+    if (!ok) break;
+    // (4) the block's levels out of TMEM, combined and scaled, into Y
+    ok = __syncthreads_and(tc_wait(&s_mbar[(g - 1) & 1], ((g - 1) >> 1) & 1));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) break;
+    {
+      const int64_t row = rb + ra;
+      const int er = sEr[ra];
+#pragma unroll 1
+      for (int c8 = 0; c8 < nh; c8 += 8) {
+        float S[TT_LEV][8];
+#pragma unroll
+        for (int l = 0; l < TT_LEV; ++l) tc_ld8(trow + l * nb + h * nh + c8, S[l]);
+        tc_ld_wait();
+        if (row < r_hi) {
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int bl = h * nh + c8 + t, b = b0 + bl;
+            if (b >= mo) continue;
+            const int fb = sFb[bl];
+            double v;
+            if (er == TT_NAN_ROW || fb < 0) {
+              v = __longlong_as_double(0x7ff8000000000000ll);
+            } else if (er <= -0x40000000 || fb == 0) {
+              v = 0.0;
+            } else {
+              const long long I = __float2ll_rn(S[0][t]) * (1ll << 24) +
+                                  __float2ll_rn(S[1][t]) * (1ll << 16) +
+                                  __float2ll_rn(S[2][t]) * (1ll << 8) + __float2ll_rn(S[3][t]);
+              const double L = (double)S[4][t] + (double)S[5][t] * 0x1p-8 +
+                               (double)S[6][t] * 0x1p-16 + (double)S[7][t] * 0x1p-24;
+              // (I + L 2^-8) 2^(E_r + E_b - 38): E_r = er - 1022 relative to the
+              // column scale, E_b = fb - 2044
+              const int p = er + fb - 2082;
+              const int p1 = max(-1022, min(1023, p / 2)), p2 = max(-1022, min(1023, p - p / 2));
+              v = fma(L, 0x1p-8, (double)I);
+              v = v * __longlong_as_double((long long)(p1 + 1023) << 52) *
+                  __longlong_as_double((long long)(p2 + 1023) << 52);
+            }
+            Y[row * ldy + b] = v;
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (!ok) {
+    // a wait ran out: this CTA's rows are NaN (the caller's next step fails)
+    for (int64_t r = r_lo + tid; r < r_hi; r += TC_THREADS)
+      for (int b = b0; b < min(mo, b0 + nb); ++b) Y[r * ldy + b] = __longlong_as_double(0x7ff8000000000000ll);
+    if (tid == 0 && err) atomicExch(err, 1);
+    // the MMAs in flight end before TMEM is released
+    if (g > 0) tc_wait(&s_mbar[(g - 1) & 1], ((g - 1) >> 1) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+}
+
 }  // namespace
+
+bool tall_tc_fits(int m, int mo) { return m >= 1 && m <= TC_M && mo >= 1 && mo <= 2 * TC_NB; }
+
+void tall_gemm_tc(const double* X, int64_t n, int m, int ldx, const double* M, int mo, double* Y,
+                  int ldy, int num_sms, int* err, cudaStream_t s) {
+  RF_CHECK(tall_tc_fits(m, mo), RAFEAST_ERR_INVALID_ARG);
+  const int nblk = (mo + TC_NB - 1) / TC_NB;
+  int nb = (mo + nblk - 1) / nblk;
+  nb = ((nb + 15) / 16) * 16;
+  const int nbx = (mo + nb - 1) / nb;
+  const int kp16 = (m + 15) & ~15, nsl = (kp16 + 31) / 32;
+  int parts = num_sms / nbx;
+  if (parts < 1) parts = 1;
+  const int64_t blocks = (n + TC_M - 1) / TC_M;
+  if (parts > blocks) parts = (int)std::max<int64_t>(1, blocks);
+  const size_t smem = 2 * (size_t)TC_DIG * TC_APLANE + (size_t)nsl * TC_DIG * nb * 64;
+  ensure_dyn_smem(reinterpret_cast<const void*>(k_tc_tall), smem);
+  dim3 grid(nbx, parts);
+  k_tc_tall<<<grid, TC_THREADS, smem, s>>>(X, n, m, ldx, M, mo, Y, ldy, nb, err);
+  RF_LAUNCH();
+}
 
 bool gram_tc_fits(int m) { return m >= 1 && m <= TC_M; }
 

@@ -70,7 +70,7 @@ EXPORTS = [
     "rafeast_get_subspace", "rafeast_solve", "rafeast_solve_batched", "rafeast_profile",
     "rafeast_last_error", "rafeast_profile_history", "rafeast_gram",
     "rafeast_gram_noalloc", "rafeast_shard_range", "rafeast_partition_instances",
-    "rafeast_solve_sharded",
+    "rafeast_solve_sharded", "rafeast_block_product",
 ]
 
 # int (*rafeast_sum_fn)(void* ctx, double* buf, int64_t count)
@@ -136,6 +136,7 @@ def load():
         "rafeast_orthonormalize": (I, [P, I, P, P]),
         "rafeast_rayleigh_ritz": (I, [P, I, P, P, P]),
         "rafeast_gram": (I, [P, I, P, P, P]),
+        "rafeast_block_product": (I, [P, I, P, P, I, P]),
         "rafeast_gram_noalloc": (I, [P, P, I64, I, P, P]),
         "rafeast_warmstart": (I, [P, D, D, I, I, I, U64]),
         "rafeast_set_subspace": (I, [P, P, I, I]),
@@ -323,6 +324,13 @@ def rafeast_gram(h, m, X, Y, G):
     """G = X^T Y; X, Y CUDA tensors (m, n) (column-major n x m), G CUDA (m, m)
     holding the column-major m x m result (G[b, a] = entry (a, b))."""
     return _check(load().rafeast_gram(h, m, _ptr(X), _ptr(Y), _ptr(G)), "rafeast_gram")
+
+
+def rafeast_block_product(h, m, X, M, mo, Y):
+    """Y = X M: X (m, n), M (mo, m) and Y (mo, n) CUDA tensors (column-major
+    n x m, m x mo and n x mo blocks)."""
+    _check(load().rafeast_block_product(h, int(m), _ptr(X), _ptr(M), int(mo), _ptr(Y)),
+           "rafeast_block_product")
 
 
 def rafeast_gram_noalloc(X, Y, n, m, G, stream=None):
