@@ -414,10 +414,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // slices); the B digits of the CTA's columns are formed once, the A digits of
 // the next 32 columns of a 128-row block while the tensor cores multiply the
 // last ones.
-constexpr int TT_LEV = 8;     // levels kept (digit pairs with i + j <= 7)
+constexpr int TT_LEV = 8;         // levels kept (digit pairs with i + j <= 7)
+constexpr int TT_THREADS = 512;   // 16 warps: four threads per row of a 128-row block
 constexpr int TT_NAN_ROW = -1000000;
+constexpr int TT_ZERO_ROW = -0x40000000;
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TT_THREADS, 1)
     k_tc_tall(const double* __restrict__ X, int64_t n, int m, int ldx,
               const double* __restrict__ Mm, int mo, double* __restrict__ Y, int ldy, int nb,
               int* __restrict__ err) {
@@ -425,7 +427,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr int ABUF = TC_DIG * TC_APLANE;  // one buffer of A digit planes (56 KB)
   const int bpl = nb * 64;                  // bytes of one B digit plane of one K slice
   unsigned char* Bp = tsm + 2 * ABUF;       // [slice][digit] planes
-  __shared__ int sCe[TC_M], sFb[TC_NB], sEr[TC_M], sEh[TC_M];
+  __shared__ int sCe[TC_M], sFb[TC_NB], sEr[TC_M];
+  // the four partial row exponents of a block live in A buffer 0, which no
+  // MMA reads while they are formed (the last block's MMAs have completed)
+  int (*sEq)[TC_M] = reinterpret_cast<int (*)[TC_M]>(tsm);
   __shared__ uint32_t s_tbase;
   __shared__ __align__(8) uint64_t s_mbar[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -434,17 +439,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int64_t r_lo = n * (int64_t)blockIdx.y / parts;
   const int64_t r_hi = n * (int64_t)(blockIdx.y + 1) / parts;
   const int kp16 = (m + 15) & ~15, nsl = (kp16 + 31) / 32;
-  // (1) column exponents of X over this CTA's rows (finite values)
-  for (int t = tid; t < TC_M; t += TC_THREADS) sCe[t] = 0;
+  // (1) column exponents of X over this CTA's rows (finite values); four
+  // threads per column, eight rows in flight each
+  for (int t = tid; t < TC_M; t += TT_THREADS) sCe[t] = 0;
   __syncthreads();
   {
-    const int a = tid & (TC_M - 1);
+    const int a = tid & (TC_M - 1), q4 = tid >> 7;
     int e = 0;
-    if (a < m)
-      for (int64_t r = r_lo + (tid >> 7); r < r_hi; r += 2) {
+    if (a < m) {
+      int64_t r = r_lo + q4;
+      for (; r + 28 < r_hi; r += 32) {
+        int ex[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          ex[u] = (int)(((unsigned long long)__double_as_longlong(X[(r + 4 * u) * ldx + a]) >> 52) & 0x7FF);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (ex[u] != 0x7FF) e = max(e, ex[u]);
+      }
+      for (; r < r_hi; r += 4) {
         const int ex = (int)(((unsigned long long)__double_as_longlong(X[r * ldx + a]) >> 52) & 0x7FF);
         if (ex != 0x7FF) e = max(e, ex);
       }
+    }
     atomicMax(&sCe[a], e);
   }
   __syncthreads();
@@ -463,7 +480,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   __syncthreads();
   // B digit planes of all K slices: scaled M^T (row b, K index a)
-  for (int e = tid; e < nb * (kp16 / 2); e += TC_THREADS) {
+  for (int e = tid; e < nb * (kp16 / 2); e += TT_THREADS) {
     const int b = e % nb, ap = e / nb, a = 2 * ap;
     const int fb = sFb[b];
     long long F0 = 0, F1 = 0;
@@ -490,23 +507,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = s_tbase;
   const uint32_t idesc = tc_idesc(nb);
-  const int ra = 32 * (warp & 3) + lane, h = warp >> 2, nh = nb >> 1;
+  // readout by warps 0..7: lane row ra, half h of the nb columns
+  const int ra = 32 * (warp & 3) + lane, h = (warp >> 2) & 1, nh = nb >> 1;
   const uint32_t trow = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+  // split mapping: row r of the block, eight of every 32 columns (quarter q4)
+  const int sr = tid & (TC_M - 1), q4 = tid >> 7;
   bool ok = true;
   int g = 0;  // K slices issued so far (buffer g & 1, its commit's phase (g >> 1) & 1)
   for (int64_t rb = r_lo; rb < r_hi && ok; rb += TC_M) {
-    // (2) row exponents of the scaled X: thread (r, half) scans the columns
-    // it will split, 16 of every 32, and the two halves are combined
+    // (2) row exponents of the scaled X over the columns this thread splits
     {
-      const int r = tid & (TC_M - 1), half = tid >> 7;
-      const int64_t row = rb + r;
-      int e = -0x40000000;
+      const int64_t row = rb + sr;
+      int e = TT_ZERO_ROW;
       bool bad = false;
       if (row < r_hi)
         for (int q = 0; q < nsl; ++q) {
-          const int a0 = 32 * q + 16 * half;
+          const int a0 = 32 * q + 8 * q4;
 #pragma unroll
-          for (int t = 0; t < 16; ++t)
+          for (int t = 0; t < 8; ++t)
             if (a0 + t < m) {
               const int ex =
                   (int)(((unsigned long long)__double_as_longlong(X[row * ldx + a0 + t]) >> 52) & 0x7FF);
@@ -514,14 +532,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               else if (ex != 0) e = max(e, ex - sCe[a0 + t]);
             }
         }
-      if (half) sEh[r] = bad ? TT_NAN_ROW : e;
+      sEq[q4][sr] = bad ? TT_NAN_ROW : e;
       __syncthreads();
-      if (!half) {
-        const int e1 = sEh[r];
-        sEr[r] = (bad || e1 == TT_NAN_ROW) ? TT_NAN_ROW : max(e, e1);
+      if (q4 == 0) {
+        int er = e;
+        bool nan = bad;
+#pragma unroll
+        for (int u = 1; u < 4; ++u) {
+          const int v = sEq[u][sr];
+          nan = nan || v == TT_NAN_ROW;
+          er = max(er, v);
+        }
+        sEr[sr] = nan ? TT_NAN_ROW : er;
       }
     }
     __syncthreads();
+    const int er_s = sEr[sr];
+    const bool on_s = rb + sr < r_hi && er_s != TT_NAN_ROW && er_s != TT_ZERO_ROW;
     // (3) K slices: digits of the next 32 columns while the last ones multiply
     for (int q = 0; q < nsl && ok; ++q, ++g) {
       const int buf = g & 1;
@@ -529,20 +556,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (g >= 2) ok = __syncthreads_and(tc_wait(&s_mbar[buf], ((g - 2) >> 1) & 1));
       if (!ok) break;
       {
-        const int r = tid & (TC_M - 1), half = tid >> 7;
-        const int64_t row = rb + r;
-        const int er = sEr[r];
-        const bool on = row < r_hi && er != TT_NAN_ROW && er > -0x40000000;
-        const int a0 = 32 * q + 16 * half;
-        double xv[16];
+        const int64_t row = rb + sr;
+        const int a0 = 32 * q + 8 * q4;
+        double xv[8];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) xv[t] = (on && a0 + t < m) ? X[row * ldx + a0 + t] : 0.0;
+        for (int t = 0; t < 8; ++t) xv[t] = (on_s && a0 + t < m) ? X[row * ldx + a0 + t] : 0.0;
 #pragma unroll
-        for (int t = 0; t < 16; t += 2) {
-          const long long F0 = xv[t] != 0.0 ? tc_fixed(xv[t], sCe[a0 + t] + er) : 0;
-          const long long F1 = xv[t + 1] != 0.0 ? tc_fixed(xv[t + 1], sCe[a0 + t + 1] + er) : 0;
-          tc_store_pair(A, TC_APLANE, tc_off(r, 16 * half + t), F0, F1);
-        }
+        for (int t = 0; t < 8; t += 2)
+          tc_store_pair(A, TC_APLANE, tc_off(sr, 8 * q4 + t), tc_fixed(xv[t], sCe[a0 + t] + er_s),
+                        tc_fixed(xv[t + 1], sCe[a0 + t + 1] + er_s));
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -572,7 +594,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     ok = __syncthreads_and(tc_wait(&s_mbar[(g - 1) & 1], ((g - 1) >> 1) & 1));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) break;
-    {
+    if (warp < 8) {
       const int64_t row = rb + ra;
       const int er = sEr[ra];
 #pragma unroll 1
@@ -590,21 +612,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             double v;
             if (er == TT_NAN_ROW || fb < 0) {
               v = __longlong_as_double(0x7ff8000000000000ll);
-            } else if (er <= -0x40000000 || fb == 0) {
+            } else if (er == TT_ZERO_ROW || fb == 0) {
               v = 0.0;
             } else {
-              const long long I = __float2ll_rn(S[0][t]) * (1ll << 24) +
-                                  __float2ll_rn(S[1][t]) * (1ll << 16) +
-                                  __float2ll_rn(S[2][t]) * (1ll << 8) + __float2ll_rn(S[3][t]);
-              const double L = (double)S[4][t] + (double)S[5][t] * 0x1p-8 +
-                               (double)S[6][t] * 0x1p-16 + (double)S[7][t] * 0x1p-24;
-              // (I + L 2^-8) 2^(E_r + E_b - 38): E_r = er - 1022 relative to the
-              // column scale, E_b = fb - 2044
+              // every level is an integer below 2^24: I = sum_{l<=3} S_l 2^(8 (3-l))
+              // and L' = sum_{l=4..7} S_l 2^(8 (7-l)) exactly in 64-bit integers,
+              // then (I + L' 2^-32) 2^(E_r + E_b - 38) with one rounding
+              const long long I = ((long long)__float2int_rn(S[0][t]) << 24) +
+                                  ((long long)__float2int_rn(S[1][t]) << 16) +
+                                  ((long long)__float2int_rn(S[2][t]) << 8) +
+                                  (long long)__float2int_rn(S[3][t]);
+              const long long Lq = ((long long)__float2int_rn(S[4][t]) << 24) +
+                                   ((long long)__float2int_rn(S[5][t]) << 16) +
+                                   ((long long)__float2int_rn(S[6][t]) << 8) +
+                                   (long long)__float2int_rn(S[7][t]);
               const int p = er + fb - 2082;
-              const int p1 = max(-1022, min(1023, p / 2)), p2 = max(-1022, min(1023, p - p / 2));
-              v = fma(L, 0x1p-8, (double)I);
-              v = v * __longlong_as_double((long long)(p1 + 1023) << 52) *
-                  __longlong_as_double((long long)(p2 + 1023) << 52);
+              v = fma((double)Lq, 0x1p-32, (double)I);
+              if (p >= -1022 && p <= 1023) {
+                v *= __longlong_as_double((long long)(p + 1023) << 52);
+              } else {
+                const int p1 = max(-1022, min(1023, p / 2)), p2 = max(-1022, min(1023, p - p / 2));
+                v = v * __longlong_as_double((long long)(p1 + 1023) << 52) *
+                    __longlong_as_double((long long)(p2 + 1023) << 52);
+              }
             }
             Y[row * ldy + b] = v;
           }
@@ -616,7 +646,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   if (!ok) {
     // a wait ran out: this CTA's rows are NaN (the caller's next step fails)
-    for (int64_t r = r_lo + tid; r < r_hi; r += TC_THREADS)
+    for (int64_t r = r_lo + tid; r < r_hi; r += TT_THREADS)
       for (int b = b0; b < min(mo, b0 + nb); ++b) Y[r * ldy + b] = __longlong_as_double(0x7ff8000000000000ll);
     if (tid == 0 && err) atomicExch(err, 1);
     // the MMAs in flight end before TMEM is released
@@ -646,7 +676,7 @@ void tall_gemm_tc(const double* X, int64_t n, int m, int ldx, const double* M, i
   const size_t smem = 2 * (size_t)TC_DIG * TC_APLANE + (size_t)nsl * TC_DIG * nb * 64;
   ensure_dyn_smem(reinterpret_cast<const void*>(k_tc_tall), smem);
   dim3 grid(nbx, parts);
-  k_tc_tall<<<grid, TC_THREADS, smem, s>>>(X, n, m, ldx, M, mo, Y, ldy, nb, err);
+  k_tc_tall<<<grid, TT_THREADS, smem, s>>>(X, n, m, ldx, M, mo, Y, ldy, nb, err);
   RF_LAUNCH();
 }
 
