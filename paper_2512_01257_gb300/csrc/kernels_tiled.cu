@@ -132,7 +132,8 @@ template <int CB, bool VF>
 __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a, TileArgs tl,
                                                                int buf) {
   if (__ldcg(&a.ctl->done)) return;
-  // [max_union * CB] staged chunks (reused for the sums), then, for the
+  // [max_union * CB] staged chunks (reused for the sums), one zero row of
+  // CB chunks (the gathers' padding entries read it), then, for the
   // deferred form, the block's shifted coefficients [CB][2][ns]
   extern __shared__ __align__(16) P4 xs[];
   __shared__ TileIdx tb;
@@ -165,7 +166,10 @@ __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a
   // the block is done)
   const bool pend = a.defer && __ldcg(&a.ctl->pend) != 0;
   const int ns = a.ns;
-  DefCoef* sdc = reinterpret_cast<DefCoef*>(xs + tl.max_union * CB);
+  // the zero row, written once (no copy reaches it)
+  const int zrow = tl.max_union;
+  if (threadIdx.x < CB) xs[zrow * CB + threadIdx.x] = P4{0ull, 0ull};
+  DefCoef* sdc = reinterpret_cast<DefCoef*>(xs + (tl.max_union + 1) * CB);
   if (pend) {
     for (int e = threadIdx.x; e < CB * 2 * ns; e += TT) {
       const int jj = e / (2 * ns), h = (e / ns) & 1, t = e % ns;
@@ -245,28 +249,29 @@ __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a
       for (int lr = rs; lr < nr; lr += NRS) {
         const int64_t row = r0 + lr;
         const int k0 = tb.srp[lr] - kbase, k1 = tb.srp[lr + 1] - kbase;
+        // eight entries at a time, all their loads in flight together; the
+        // entries past the row's end read the zero row and add +0 (the sum
+        // starts at +0 and is never -0, so this leaves it unchanged: the
+        // same sum, entry by entry in CSR order, as without padding)
         P4 acc = {0ull, 0ull};
-        int k = k0;
-        for (; k + 4 <= k1; k += 4) {
-          const P4 x0 = xs[slx[k] * CB + j], x1 = xs[slx[k + 1] * CB + j];
-          const P4 x2 = xs[slx[k + 2] * CB + j], x3 = xs[slx[k + 3] * CB + j];
+        for (int k = k0; k < k1; k += 8) {
+          int id[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) id[e] = k + e < k1 ? (int)slx[k + e] : zrow;
+          P4 x[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x[e] = xs[id[e] * CB + j];
           if constexpr (VF) {
-            acc = p4add(acc, x0);
-            acc = p4add(acc, x1);
-            acc = p4add(acc, x2);
-            acc = p4add(acc, x3);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc = p4add(acc, x[e]);
           } else {
             const float* v = a.val + kbase + k;
-            acc = p4fma(splat2(__ldg(v)), x0, acc);
-            acc = p4fma(splat2(__ldg(v + 1)), x1, acc);
-            acc = p4fma(splat2(__ldg(v + 2)), x2, acc);
-            acc = p4fma(splat2(__ldg(v + 3)), x3, acc);
+            float vv[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) vv[e] = k + e < k1 ? __ldg(v + e) : 0.0f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc = p4fma(splat2(vv[e]), x[e], acc);
           }
-        }
-        for (; k < k1; ++k) {
-          const P4 x0 = xs[slx[k] * CB + j];
-          if constexpr (VF) acc = p4add(acc, x0);
-          else acc = p4fma(splat2(__ldg(a.val + kbase + k)), x0, acc);
         }
         const P4 rv = xs[(us + lr) * CB + j];
         const float2 r2[2] = {lo2(rv.lo), lo2(rv.hi)};
@@ -408,7 +413,7 @@ template <int CB, bool VF>
 static void launch_cb(const CocgArgs<float>& a, const TileArgs& tl, int buf, int num_sms,
                       int occ_cap, cudaStream_t s) {
   auto kern = k_ms_dots_tiled<CB, VF>;
-  const size_t stage = (size_t)tl.max_union * CB * sizeof(float4);
+  const size_t stage = (size_t)(tl.max_union + 1) * CB * sizeof(float4);
   const size_t red = std::max((size_t)TT * 10 * sizeof(double),
                               2 * CB * 5 * sizeof(double) + 2 * CB * sizeof(MsSeed));
   const size_t coef = a.defer ? (size_t)CB * 2 * a.ns * sizeof(DefCoef) : 0;
