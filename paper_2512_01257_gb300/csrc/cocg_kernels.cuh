@@ -266,7 +266,7 @@ __device__ __forceinline__ void cocg_dots_body(const CocgArgs<T>& a, const CocgA
         for (int j = 0; j < NC; ++j) acc[c][j] = mk<T>((T)0, (T)0);
       // float kernels with at most 2 chunks per lane have the registers to
       // keep 4 entries' loads in flight
-      constexpr int NB = (sizeof(T) == 4 && MAXCPL <= 2) ? 4 : 2;
+      constexpr int NB = sizeof(T) == 4 ? (MAXCPL == 1 ? 8 : MAXCPL == 2 ? 4 : 2) : 2;
       if constexpr (VF)
         gather_row_vf<T, NC, MAXCPL, NB>(a.lcolidx, k0, k1, (int)row, mp.lg, mp.G, gmask, R,
                                          ldt, coff, mask, acc);

@@ -146,19 +146,26 @@ __device__ __forceinline__ long long tc_fixed(double x, int ebias) {
   return (b >> 63) ? -F : F;
 }
 
-// balanced base-256 digits, d[0] most significant
+// balanced base-256 digits of |F| <= 2^55, d[0] most significant: the bytes
+// of the two's complement, low to high, each moved into [-128, 128) by a
+// carry into the next (32-bit operations on the two halves of F)
 __device__ __forceinline__ void tc_digits(long long F, int (&d)[TC_DIG]) {
+  const unsigned lo = (unsigned)(unsigned long long)F;
+  const int hi = (int)(F >> 32);
+  int c = 0;
 #pragma unroll
-  for (int i = TC_DIG - 1; i > 0; --i) {
-    int v = (int)(F & 255);
-    F >>= 8;
-    if (v >= 128) {
-      v -= 256;
-      F += 1;
-    }
-    d[i] = v;
+  for (int i = TC_DIG - 1; i >= 3; --i) {
+    const int v = (int)((lo >> (8 * (TC_DIG - 1 - i))) & 255u) + c;
+    c = v >= 128;
+    d[i] = v - (c << 8);
   }
-  d[0] = (int)F;
+#pragma unroll
+  for (int i = 2; i >= 1; --i) {
+    const int v = (int)(((unsigned)hi >> (8 * (2 - i))) & 255u) + c;
+    c = v >= 128;
+    d[i] = v - (c << 8);
+  }
+  d[0] = (hi >> 16) + c;
 }
 
 // two values at consecutive k of one row into the 7 digit planes (one 32-bit
