@@ -1707,9 +1707,11 @@ int rafeast_create(rafeast_t* out, int64_t n, int64_t nnz, const int32_t* row_pt
     h->norm1 = norm1 > 0.0 ? norm1 : 1.0;
     h->glo = glo;
     h->ghi = ghi;
-    // row order. Default: recursive breadth-first bisection when its row
-    // tiles gather from at least 15% fewer rows than the caller's order
-    // (tiling.cpp); RAFEAST_CREATE_RCM: reverse Cuthill-McKee when it
+    // row order. Default: recursive breadth-first bisection, down to sets of
+    // one tile's rows (each kept in its level-structure order: finer cuts
+    // gave tiles with larger unions), when its row tiles gather from at
+    // least 15% fewer rows than the caller's order (tiling.cpp);
+    // RAFEAST_CREATE_RCM: reverse Cuthill-McKee when it
     // narrows the band by 30%; FORCE_REORDER applies the chosen kind always
     std::vector<int32_t> perm;
     bool reorder = false;
@@ -1721,7 +1723,7 @@ int rafeast_create(rafeast_t* out, int64_t n, int64_t nnz, const int32_t* row_pt
         reorder = (flags & RAFEAST_CREATE_FORCE_REORDER) || (double)bw1 < 0.7 * (double)bw0;
         h->order_kind = reorder ? 2 : 0;
       } else {
-        bisect_order(n, rp.data(), ci.data(), 32, perm);
+        bisect_order(n, rp.data(), ci.data(), TILE_TMAX, perm);
         bool better = (flags & RAFEAST_CREATE_FORCE_REORDER) != 0;
         if (!better) {
           // the permuted pattern (indices only) for the comparison
