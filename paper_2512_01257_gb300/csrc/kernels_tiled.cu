@@ -354,16 +354,36 @@ __global__ void __launch_bounds__(TT, TT_MINB) k_ms_dots_tiled(CocgArgs<float> a
   MsSeed* s_seed = reinterpret_cast<MsSeed*>(s_acc + 2 * CB * 5);
   {
     // value v = (pair jj, sum t): lane l adds the CTAs l, l + 32, ... of the
-    // block in that order, then the warp adds its lanes by a fixed tree
+    // block in that order, then the warp adds its lanes by a fixed tree. A
+    // warp takes the values warp, warp + TT/32, ...; the loads of all of them
+    // are issued before any is added.
+    constexpr int NW = TT / 32, VPW = (CB * 10 + NW - 1) / NW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int v = warp; v < CB * 10; v += TT / 32) {
-      const int jj = v / 10, t = v % 10;
-      double sv = 0.0;
-      for (int b = lane; b < per_block; b += 32)
-        sv += __ldcg(tl.part + ((int64_t)(cbk + b * ncb) * CB + jj) * 10 + t);
+    double sv[VPW];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-      if (lane == 0) s_acc[5 * (2 * jj + t / 5) + t % 5] = sv;
+    for (int u = 0; u < VPW; ++u) sv[u] = 0.0;
+    for (int b0 = 0; b0 < per_block; b0 += 32) {
+      const int b = b0 + lane;
+      double pv[VPW];
+#pragma unroll
+      for (int u = 0; u < VPW; ++u) {
+        const int v = warp + NW * u;
+        pv[u] = (v < CB * 10 && b < per_block)
+                    ? __ldcg(tl.part + ((int64_t)(cbk + b * ncb) * CB + v / 10) * 10 + v % 10)
+                    : 0.0;
+      }
+      if (b < per_block) {
+#pragma unroll
+        for (int u = 0; u < VPW; ++u) sv[u] += pv[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < VPW; ++u) {
+      const int v = warp + NW * u;
+      double x = sv[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0 && v < CB * 10) s_acc[5 * (2 * (v / 10) + (v % 10) / 5) + (v % 10) % 5] = x;
     }
   }
   __shared__ MsCount cnt;
