@@ -260,9 +260,10 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sample_ms, "ms_per_solve_extrapolated": est * 1e3,
-            "higher_is_better": True, "scaling": "weak",
+            "higher_is_better": True,
+            "scaling": "weak" if args.shard == "replicas" else "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(key),
+            "config": dict(_config(key), parallelism="the oracle on the host cores (rank 0)"),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -293,9 +294,10 @@ def _run_reference_sbm(args):
     value = len(insts) / est
     line = {"metric": METRIC, "value": value, "unit": "problems/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "sbm64: 64 stochastic-block-model Laplacians, batched"},
+            "config": {"workload": "sbm64: 64 stochastic-block-model Laplacians, batched",
+                       "parallelism": "the oracle on the host cores (rank 0)"},
             "cpu_baseline": {"value": value, "unit": "problems/s", "cores": 1, "kind": "oracle",
                              "sample": ests[0]["sample"]},
             "e2e": {"value": value, "unit": "problems/s", "h2d_bytes_per_step": 0,
@@ -989,6 +991,20 @@ def main():
         line["vs_baseline"] = value * 72.4
         line["vs_baseline_source"] = ("paper Table 1, RA-FEAST (N_c=2) at n=16,000: 72.4 s per "
                                       "solve, single-threaded CPU, FEAST v4 direct solves")
+    # the eigenspace of the last timed solve: Davis-Kahan in the spectral norm,
+    # ||sin Theta||_2 <= ||A V - V diag(lam)||_2 / delta, delta the distance of
+    # the returned values to the nearest eigenvalue outside the interval (the
+    # stored spectrum); host FP64, outside the timed region
+    if mf == len(ref) and g.get("neighbours"):
+        vec = evecs[:mf].cpu().numpy().T
+        a_sp = lap.scipy()
+        res_blk = a_sp @ vec - vec * ev
+        r2 = float(np.sqrt(max(np.linalg.eigvalsh(res_blk.T @ res_blk).max(), 0.0)))
+        delta = float(min(abs(o - ev).min() for o in g["neighbours"][:1]))
+        line["parity"]["sin_theta_bound"] = r2 / delta
+        line["parity"]["sin_theta_gate"] = 1e-6 if prec == R.RAFEAST_MIXED else 1e-8
+        line["parity"]["sin_theta_how"] = ("Davis-Kahan: ||A V - V diag(lam)||_2 / gap to the "
+                                           "nearest eigenvalue outside the interval")
     if key.startswith("rgg"):
         line["parity"]["max_abs_err_vs_arpack"] = (float(np.max(np.abs(np.sort(ev) - ref)))
                                                    if mf == len(ref) else None)
