@@ -673,7 +673,7 @@ static void jacobi_launch(const double* A, int m, double* w, double* V, T* Vg, i
   size_t smem = (size_t)me * me * sizeof(T);
   if (2 * smem <= JACOBI_SMEM_MAX) smem *= 2;  // V beside A
   ensure_dyn_smem(reinterpret_cast<const void*>(k_jacobi<T>), smem);
-  k_jacobi<T><<<1, 512, smem, s>>>(A, m, w, V, Vg, sweeps, rot_tol, off_tol);
+  k_jacobi<T><<<1, 1024, smem, s>>>(A, m, w, V, Vg, sweeps, rot_tol, off_tol);
   RF_LAUNCH();
 }
 
