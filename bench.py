@@ -12,7 +12,7 @@ reports the same 64 problems solved one at a time by rafeast_solve.
 Default workload (``knn200k``): kNN graph Laplacian of 200,000 uniform points
 in [0,1]^3 (seed 2), k = 10, union-symmetrised, unit weights, + 1e-3 I; the
 64 smallest eigenvalues; m0 = 80, N_c = 4, p = 20, q = 2, outer tolerance
-1e-11, relaxed inner solves (COCG tolerance 1e-2, at most 100 steps), mixed
+1e-11, relaxed inner solves (COCG tolerance 1e-2, at most 60 steps), mixed
 precision (float32 shifted solves, double outer loop). Every timed step
 starts with a cold L2 (a 512 MB write before it, outside its CUDA events).
 
@@ -322,7 +322,7 @@ def _config(key):
     g = CF.load_golden()[key]
     return {"workload": f"{key}: {cfg.description}", "n": g["n"], "nnz": g["nnz"],
             "count": g["count"], "m0": cfg.m0, "nc": cfg.nc, "p": cfg.p, "q": cfg.q,
-            "solve_tol": cfg.solve_tol, "outer_tol": cfg.outer_tol,
+            "solve_tol": cfg.solve_tol, "max_inner": cfg.max_inner, "outer_tol": cfg.outer_tol,
             "interval": [g["lmin"], g["lmax"]],
             "l2": "L2 flushed (512 MB write, outside the timed events) before every timed step"}
 
