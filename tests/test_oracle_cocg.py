@@ -71,3 +71,14 @@ def test_iteration_cap():
     b = np.ones(200)
     res = C.cocg(lambda x: a @ x, 1.0 + 1e-3j, b, 1e-14, 3)
     assert res.iters[0] == 3 and not res.converged[0]
+
+
+def test_bdot_is_unconjugated():
+    # u^T v without conjugation: (1 + 2i) * (3 - i) + 1j * 1j = 5 + 5i - 1
+    u = np.array([[1 + 2j], [1j]])
+    v = np.array([[3 - 1j], [1j]])
+    assert np.allclose(C.bdot(u, v), [4 + 5j])
+    # column by column
+    u2 = np.hstack([u, 2 * u])
+    v2 = np.hstack([v, v])
+    assert np.allclose(C.bdot(u2, v2), [4 + 5j, 8 + 10j])

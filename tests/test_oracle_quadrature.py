@@ -89,3 +89,15 @@ def test_rejects_bad_arguments():
         Q.nodes(0.0, 1.0, 0)
     with pytest.raises(ValueError):
         Q.nodes(0.0, 1.0, 2, 1.5)
+
+
+def test_gauss_legendre_three_point_rule():
+    # the textbook 3-point rule: nodes 0, +-sqrt(3/5), weights 8/9, 5/9; it
+    # integrates polynomials up to degree 5 exactly
+    x, om = Q.gauss_legendre(3)
+    order = np.argsort(x)
+    assert np.allclose(x[order], [-np.sqrt(0.6), 0.0, np.sqrt(0.6)], atol=1e-15)
+    assert np.allclose(om[order], [5 / 9, 8 / 9, 5 / 9], atol=1e-15)
+    for deg in range(6):
+        exact = (1.0 - (-1.0) ** (deg + 1)) / (deg + 1)
+        assert abs(np.sum(om * x ** deg) - exact) <= 1e-14
